@@ -1,0 +1,240 @@
+"""FP64 CPU oracle for the phase-field no-slip DPD time step (arXiv:1807.09896).
+
+TEST INFRASTRUCTURE ONLY.  This package exists so that the tests, the smoke
+check and the benchmark's CPU-baseline leg can check the CUDA library against a
+plain, slow, obviously correct restatement of the paper.  Nothing in the product
+path imports it, and it imports nothing from the product package.
+
+The arithmetic lives in ``dpd_oracle.c`` (built by ``oracle/build.py``); this
+module only marshals numpy arrays into it.  Citations:
+
+* pair noise ``xi_ij`` (Eq. 7): Philox4x32-10 + Box-Muller, ``philox``/``xi``;
+* pair force (Eqs. 3-10): ``forces``;
+* time step (Sec. II.A integrator, ref. 35) with bounce-back reflection
+  (Sec. II.C, Eq. 17, Fig. 4): ``step``;
+* particle phase field by trilinear interpolation (Sec. II.C): ``phi_at``;
+* velocity-profile sums (Sec. III.A): ``profile``.
+
+Parity status of each function is recorded at the top of ``dpd_oracle.c`` and in
+the tests under ``tests/test_oracle_*.py``.  The absolute viscosity of the 3-D
+fluid is "parity unpinned": the paper prints only 2-D values.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+_P_NAMES = [
+    "Lx", "Ly", "Lz", "a_ff", "a_fs", "a_sf", "a_ss", "gamma", "sigma", "kBT", "dt",
+    "lam", "gx", "gy", "gz", "vwx", "vwy", "vwz", "reflect_variant",
+]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u32p = np.ctypeslib.ndpointer(np.uint32, flags="C")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C")
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C")
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_philox4x32_10.restype = None
+        L.or_u01.argtypes = [ctypes.c_uint32]
+        L.or_u01.restype = ctypes.c_double
+        L.or_xi.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                            ctypes.c_uint64]
+        L.or_xi.restype = ctypes.c_double
+        L.or_phi_at.argtypes = [f32p, i32p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double]
+        L.or_phi_at.restype = ctypes.c_double
+        L.or_pairs.argtypes = [ctypes.c_int, f64p, f64p, ctypes.c_int, ctypes.c_long, i32p]
+        L.or_pairs.restype = ctypes.c_long
+        L.or_forces.argtypes = [ctypes.c_int, f64p, f64p, i32p, u8p, f64p, ctypes.c_uint32,
+                                ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, f64p]
+        L.or_forces.restype = ctypes.c_int
+        L.or_step.argtypes = [ctypes.c_int, f64p, f64p, f64p, i32p, u8p, f64p, f32p, i32p,
+                              ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                              ctypes.c_int, u8p, i64p]
+        L.or_step.restype = ctypes.c_int
+        L.or_profile.argtypes = [ctypes.c_int, f32p, f64p, u8p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_double, f64p]
+        L.or_profile.restype = None
+        L.or_num_threads.argtypes = []
+        L.or_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Params:
+    """Physical and numerical parameters of one DPD system (DPD units, r_c = m = 1)."""
+
+    box: tuple = (10.0, 10.0, 12.0)
+    a_ff: float = 25.0
+    a_fs: float = 25.0
+    gamma: float = 4.5
+    sigma: float = 3.0
+    kBT: float = 1.0
+    dt: float = 0.01
+    lam: float = 0.65
+    g: tuple = (0.0, 0.0, 0.0)
+    v_wall: tuple = (0.0, 0.0, 0.0)
+    reflect_variant: int = 0
+    seed: int = 0
+    sys: int = 0
+
+    def flat(self) -> np.ndarray:
+        v = [*self.box, self.a_ff, self.a_fs, self.a_fs, 0.0, self.gamma, self.sigma, self.kBT,
+             self.dt, self.lam, *self.g, *self.v_wall, float(self.reflect_variant)]
+        assert len(v) == len(_P_NAMES)
+        return np.asarray(v, dtype=np.float64)
+
+
+@dataclass
+class Field:
+    """Phase field on a periodic grid: node (i, j, k) sits at (i, j, k) * h."""
+
+    grid: np.ndarray  # float32, shape (nz, ny, nx), x fastest
+    h: float
+
+    @property
+    def dims(self) -> np.ndarray:
+        nz, ny, nx = self.grid.shape
+        return np.asarray([nx, ny, nz], dtype=np.int32)
+
+
+@dataclass
+class State:
+    """Particle state in id order: r, v, pair force f (without the body force)."""
+
+    pos: np.ndarray
+    vel: np.ndarray
+    frc: np.ndarray
+    id: np.ndarray
+    type: np.ndarray
+    step: int = 0
+    stats: dict = field(default_factory=lambda: {"reflections": 0, "fallbacks": 0})
+
+    def copy(self) -> "State":
+        return State(self.pos.copy(), self.vel.copy(), self.frc.copy(), self.id.copy(),
+                     self.type.copy(), self.step, dict(self.stats))
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one 128-bit counter under one 64-bit key."""
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_c(ctr, np.uint32), _c(key, np.uint32), out)
+    return out
+
+
+def u01(x: int) -> float:
+    return lib().or_u01(int(x) & 0xFFFFFFFF)
+
+
+def xi(id_a: int, id_b: int, step: int, sys: int, seed: int) -> float:
+    """Gaussian pair noise of Eq. 7 for the pair (id_a, id_b) at `step`."""
+    return lib().or_xi(id_a, id_b, step, sys, seed)
+
+
+def phi_at(f: Field, pts) -> np.ndarray:
+    """Trilinear periodic interpolation of the phase field at points (n, 3)."""
+    pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+    g = _c(f.grid, np.float32).reshape(-1)
+    d = f.dims
+    L = lib()
+    return np.array([L.or_phi_at(g, d, f.h, p[0], p[1], p[2]) for p in pts])
+
+
+def pairs(pos, box, method: int = 0) -> np.ndarray:
+    """All unordered pairs (i < j) closer than r_c = 1, lexicographic rows."""
+    pos = _c(pos, np.float64)
+    n = len(pos)
+    L = _c(box, np.float64)
+    cap = max(16, n * 64)
+    out = np.zeros(2 * cap, np.int32)
+    m = lib().or_pairs(n, pos.reshape(-1), L, method, cap, out)
+    if m < 0:
+        raise ValueError("box too small for the cell list (each edge must be >= 3 r_c)")
+    if m > cap:
+        raise RuntimeError("pair buffer too small")
+    return out[: 2 * m].reshape(m, 2)
+
+
+def forces(pos, vt, ids, types, p: Params, step: int, method: int = 1) -> np.ndarray:
+    """Total pair force on every particle (Eq. 2) at predicted velocities vt."""
+    pos = _c(pos, np.float64)
+    n = len(pos)
+    f = np.zeros((n, 3), np.float64)
+    rc = lib().or_forces(n, pos.reshape(-1), _c(vt, np.float64).reshape(-1), _c(ids, np.int32),
+                         _c(types, np.uint8), p.flat(), step, p.sys, p.seed, method,
+                         f.reshape(-1))
+    if rc != 0:
+        raise RuntimeError(f"or_forces failed ({rc})")
+    return f
+
+
+def init_forces(s: State, p: Params, method: int = 1) -> State:
+    """f(0): the pair force at the initial state, with the predicted velocity equal to v(0)."""
+    s = s.copy()
+    vt = s.vel.copy()
+    vt[s.type != 0] = np.asarray(p.v_wall)
+    s.frc = forces(s.pos, vt, s.id, s.type, p, s.step, method)
+    return s
+
+
+def step(s: State, p: Params, f: Field, method: int = 1, return_reflected: bool = False):
+    """Advance the state by one time step; the new force uses counter step+1."""
+    s = s.copy()
+    n = len(s.pos)
+    refl = np.zeros(n, np.uint8)
+    stats = np.zeros(2, np.int64)
+    pos = _c(s.pos, np.float64)
+    vel = _c(s.vel, np.float64)
+    frc = _c(s.frc, np.float64)
+    rc = lib().or_step(n, pos.reshape(-1), vel.reshape(-1), frc.reshape(-1), _c(s.id, np.int32),
+                       _c(s.type, np.uint8), p.flat(), _c(f.grid, np.float32).reshape(-1),
+                       f.dims, f.h, s.step + 1, p.sys, p.seed, method, refl, stats)
+    if rc != 0:
+        raise RuntimeError(f"or_step failed ({rc})")
+    s.pos, s.vel, s.frc = pos, vel, frc
+    s.step += 1
+    s.stats = {"reflections": s.stats["reflections"] + int(stats[0]),
+               "fallbacks": s.stats["fallbacks"] + int(stats[1])}
+    if return_reflected:
+        return s, refl.astype(bool)
+    return s
+
+
+def profile(pos_f32, vel, types, axis: int, nbins: int, lo: float, hi: float,
+            out: np.ndarray | None = None) -> np.ndarray:
+    """Per-bin {count, sum vx, sum vy, sum vz, sum |v|^2} over fluid particles.
+
+    ``pos_f32`` are binary32 positions (the bin decision is taken in binary32).
+    """
+    if out is None:
+        out = np.zeros((nbins, 5), np.float64)
+    pos4 = np.zeros((len(pos_f32), 4), np.float32)
+    pos4[:, :3] = np.asarray(pos_f32, dtype=np.float32)[:, :3]
+    lib().or_profile(len(pos4), pos4.reshape(-1), _c(vel, np.float64).reshape(-1),
+                     _c(types, np.uint8), axis, nbins, lo, hi, out.reshape(-1))
+    return out
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()

@@ -1,0 +1,197 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's tests and the benchmark.
+
+This module holds no arithmetic of the method itself: it only draws particle
+positions and velocities and tabulates the phase field phi(x) on a grid.  The
+phase field is an input of the method; every workload here uses the steady
+planar profile of Eq. 14, phi = tanh(d / (sqrt(2) eps)) with d the signed
+distance to the solid surface (positive in the fluid) and eps = 0.5, sampled on a
+grid of spacing 0.25 r_c (Sec. II.B).
+
+Workloads (DPD units, r_c = 1, rho = 3):
+
+* ``channel(Lx, Ly, H)`` -- a plane channel of fluid gap H between walls at
+  z = 0 and z = H.  The box is periodic with Lz = H + 2: a 1 r_c solid layer
+  sits below z = 0 (wrapped to z in [H + 1, H + 2)) and above z = H, and the two
+  layers meet through the periodic wrap, so the fluid sees walls only.
+  Fluid particles are uniform in the gap, solid particles uniform in the
+  layers (the paper's frozen boundary particles, Sec. II.C).
+* ``bulk(L)`` -- a periodic box with no solid (phi = 1 everywhere).
+* ``sphere_pack(L, nspheres, rmin, rmax)`` -- a periodic cube holding
+  non-overlapping solid spheres; fluid in the pore space, a 1 r_c solid shell
+  inside each surface.
+
+Velocities are Maxwellian at k_BT with the mean removed; solid particles are at
+rest.  Every array is a deterministic function of the seed (numpy PCG64).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+EPS = 0.5      # interface parameter of Eq. 14 used by every workload
+GRID_H = 0.25  # phase-field grid spacing
+
+
+@dataclass
+class Workload:
+    name: str
+    box: tuple          # (Lx, Ly, Lz)
+    phi: np.ndarray     # float32 (nz, ny, nx), node (i, j, k) at (i, j, k) * h
+    h: float
+    pos: np.ndarray     # float32 (n, 3)
+    vel: np.ndarray     # float32 (n, 3)
+    id: np.ndarray      # int32 (n,), a permutation of 0..n-1
+    type: np.ndarray    # uint8 (n,), 0 fluid, 1 solid
+    gap: float = 0.0    # channel gap H (0 if not a channel)
+
+    @property
+    def n(self) -> int:
+        return len(self.pos)
+
+    @property
+    def n_fluid(self) -> int:
+        return int((self.type == 0).sum())
+
+    @property
+    def n_solid(self) -> int:
+        return int((self.type != 0).sum())
+
+    def pos4(self) -> np.ndarray:
+        p = np.zeros((self.n, 4), np.float32)
+        p[:, :3] = self.pos
+        return p
+
+    def vel4(self) -> np.ndarray:
+        v = np.zeros((self.n, 4), np.float32)
+        v[:, :3] = self.vel
+        return v
+
+
+def _phi_from_distance(d: np.ndarray) -> np.ndarray:
+    return np.tanh(d / (math.sqrt(2.0) * EPS)).astype(np.float32)
+
+
+def _grid_dims(box, h):
+    dims = []
+    for L in box:
+        n = int(round(L / h))
+        if abs(n * h - L) > 1e-9 * max(1.0, L):
+            raise ValueError(f"box edge {L} is not a whole number of grid spacings {h}")
+        dims.append(n)
+    return dims
+
+
+def _maxwell(rng, n, kBT):
+    v = rng.normal(0.0, math.sqrt(kBT), size=(n, 3))
+    if n:
+        v -= v.mean(axis=0)
+    return v
+
+
+def _finish(name, box, phi, h, fpos, spos, kBT, rng, gap=0.0, shuffle_ids=True):
+    nf, ns = len(fpos), len(spos)
+    pos = np.concatenate([fpos, spos]).astype(np.float32)
+    # Clamp any coordinate that rounds up to the box edge in binary32.
+    for a in range(3):
+        col = pos[:, a]
+        col[col >= np.float32(box[a])] = np.nextafter(np.float32(box[a]), np.float32(0))
+        col[col < 0] = 0
+    vel = np.zeros((nf + ns, 3), np.float64)
+    vel[:nf] = _maxwell(rng, nf, kBT)
+    types = np.concatenate([np.zeros(nf, np.uint8), np.ones(ns, np.uint8)])
+    ids = rng.permutation(nf + ns).astype(np.int32) if shuffle_ids else np.arange(nf + ns, dtype=np.int32)
+    # Store in id order so that state arrays index by id.
+    order = np.argsort(ids)
+    return Workload(name, tuple(float(b) for b in box), phi, h, pos[order],
+                    vel[order].astype(np.float32), ids[order], types[order], gap)
+
+
+def channel(Lx: float, Ly: float, H: float, rho: float = 3.0, layer: float = 1.0,
+            kBT: float = 1.0, seed: int = 0, h: float = GRID_H) -> Workload:
+    """Plane Poiseuille channel: fluid gap (0, H), solid layers of `layer` r_c."""
+    box = (float(Lx), float(Ly), float(H + 2 * layer))
+    nx, ny, nz = _grid_dims(box, h)
+    z = np.arange(nz) * h
+    d = np.where(z <= H, np.minimum(z, H - z), -np.minimum(z - H, box[2] - z))
+    phi_z = _phi_from_distance(d)
+    phi = np.broadcast_to(phi_z[:, None, None], (nz, ny, nx)).astype(np.float32).copy()
+    rng = np.random.default_rng(seed)
+    nf = int(round(rho * Lx * Ly * H))
+    ns = int(round(rho * Lx * Ly * 2 * layer))
+    fz = rng.uniform(0.0, H, size=nf)
+    fz[fz == 0.0] = H / 2
+    fpos = np.stack([rng.uniform(0, Lx, nf), rng.uniform(0, Ly, nf), fz], axis=1)
+    spos = np.stack([rng.uniform(0, Lx, ns), rng.uniform(0, Ly, ns),
+                     H + rng.uniform(0.0, 2 * layer, ns)], axis=1)
+    return _finish(f"channel_{Lx:g}x{Ly:g}x{H:g}", box, phi, h, fpos, spos, kBT, rng, gap=H)
+
+
+def bulk(L, rho: float = 3.0, kBT: float = 1.0, seed: int = 0, h: float = GRID_H) -> Workload:
+    """Periodic box of fluid with no solid anywhere (phi = 1)."""
+    box = tuple(float(x) for x in (L if np.ndim(L) else (L, L, L)))
+    nx, ny, nz = _grid_dims(box, h)
+    phi = np.ones((nz, ny, nx), np.float32)
+    rng = np.random.default_rng(seed)
+    nf = int(round(rho * box[0] * box[1] * box[2]))
+    fpos = rng.uniform(0, 1, size=(nf, 3)) * np.asarray(box)
+    return _finish(f"bulk_{box[0]:g}x{box[1]:g}x{box[2]:g}", box, phi, h, fpos,
+                   np.zeros((0, 3)), kBT, rng)
+
+
+def _place_spheres(L, nsph, rmin, rmax, rng, max_tries=200000):
+    cs, rs = [], []
+    tries = 0
+    while len(cs) < nsph:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place the requested spheres")
+        c = rng.uniform(0, L, 3)
+        r = rng.uniform(rmin, rmax)
+        ok = True
+        for c2, r2 in zip(cs, rs):
+            d = c - c2
+            d -= L * np.round(d / L)
+            if np.linalg.norm(d) < r + r2:
+                ok = False
+                break
+        if ok:
+            cs.append(c)
+            rs.append(r)
+    return np.asarray(cs), np.asarray(rs)
+
+
+def _sphere_distance(pts, cs, rs, L):
+    d = np.full(len(pts), np.inf)
+    for c, r in zip(cs, rs):
+        dd = pts - c
+        dd -= L * np.round(dd / L)
+        d = np.minimum(d, np.sqrt((dd * dd).sum(axis=1)) - r)
+    return d
+
+
+def sphere_pack(L: float, nspheres: int, rmin: float, rmax: float, rho: float = 3.0,
+                layer: float = 1.0, kBT: float = 1.0, seed: int = 0,
+                h: float = GRID_H) -> Workload:
+    """Periodic cube of non-overlapping solid spheres; fluid fills the pores."""
+    box = (float(L),) * 3
+    rng = np.random.default_rng(seed)
+    cs, rs = _place_spheres(L, nspheres, rmin, rmax, rng)
+    n = int(round(L / h))
+    phi = np.empty((n, n, n), np.float32)
+    ax = np.arange(n) * h
+    yy, xx = np.meshgrid(ax, ax, indexing="ij")
+    plane = np.stack([xx.ravel(), yy.ravel(), np.zeros(xx.size)], axis=1)
+    for k in range(n):
+        plane[:, 2] = k * h
+        phi[k] = _phi_from_distance(_sphere_distance(plane, cs, rs, L)).reshape(n, n)
+    ncand = int(round(rho * L ** 3))
+    cand = rng.uniform(0, L, size=(ncand, 3))
+    d = np.empty(ncand)
+    chunk = 1 << 18
+    for s in range(0, ncand, chunk):
+        d[s:s + chunk] = _sphere_distance(cand[s:s + chunk], cs, rs, L)
+    fpos = cand[d > 0]
+    spos = cand[(d <= 0) & (d >= -layer)]
+    return _finish(f"spheres_{L:g}_{nspheres}", box, phi, h, fpos, spos, kBT, rng)

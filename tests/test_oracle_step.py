@@ -1,0 +1,221 @@
+"""Pins of the oracle's time step: integrator (Sec. II.A, ref. 35), phase-field
+interpolation and bounce-back reflection (Sec. II.C, Eq. 17, Fig. 4), and the
+profile sums (Sec. III.A).
+
+* ballistic motion under the body force alone is exact: r = r0 + v0 t + g t^2/2;
+* with only conservative forces and lambda = 1/2 the total energy error of the
+  velocity-Verlet scheme is second order in dt (halving dt quarters it);
+* the fluctuation-dissipation pair gamma = sigma^2 / 2 k_BT (Eq. 8) holds the
+  kinetic temperature at k_BT (Sec. III.A: deviations measure integration error);
+* trilinear interpolation returns node values and reproduces affine fields;
+* a particle crossing a planar phi = 0 surface is put back at the mirror point of
+  its would-be position (Fig. 4: phi_bb ~ -phi(t+dt)), with all velocity
+  components reversed and no closing half-kick; a mirror point that is itself in
+  the solid sends the particle back to r(t);
+* no fluid particle ends a step at phi < 0 (Sec. II.C), frozen particles stay put.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_09896_gb300 import inputs
+
+
+def _state(w, vel=None):
+    s = oracle.State(w.pos.astype(np.float64), (w.vel if vel is None else vel).astype(np.float64),
+                     np.zeros((w.n, 3)), w.id.copy(), w.type.copy())
+    return s
+
+
+def _field(w):
+    return oracle.Field(w.phi, w.h)
+
+
+def test_ballistic_motion_under_body_force_is_exact():
+    w = inputs.bulk(4.0, seed=1)
+    g = (0.3, -0.2, 0.05)
+    p = oracle.Params(box=w.box, a_ff=0.0, gamma=0.0, sigma=0.0, g=g, dt=0.02)
+    s = oracle.init_forces(_state(w), p)
+    r0, v0 = s.pos.copy(), s.vel.copy()
+    for _ in range(25):
+        s = oracle.step(s, p, _field(w))
+    t = 25 * p.dt
+    expect = r0 + v0 * t + 0.5 * np.asarray(g) * t * t
+    L = np.asarray(w.box)
+    d = s.pos - expect
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < 1e-12
+    np.testing.assert_allclose(s.vel, v0 + np.asarray(g) * t, rtol=0, atol=1e-13)
+
+
+def _energy(s, p):
+    ke = 0.5 * (s.vel ** 2).sum()
+    pairs = oracle.pairs(s.pos, p.box, method=1)
+    L = np.asarray(p.box)
+    d = s.pos[pairs[:, 0]] - s.pos[pairs[:, 1]]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(1))
+    return ke + (0.5 * p.a_ff * (1 - r) ** 2).sum()
+
+
+def _energy_error(dt, T=1.0):
+    w = inputs.bulk(4.0, seed=2)
+    p = oracle.Params(box=w.box, a_ff=25.0, gamma=0.0, sigma=0.0, dt=dt, lam=0.5)
+    s = oracle.init_forces(_state(w), p)
+    e0 = _energy(s, p)
+    err = 0.0
+    for _ in range(int(round(T / dt))):
+        s = oracle.step(s, p, _field(w))
+        err = max(err, abs(_energy(s, p) - e0))
+    return err / e0
+
+
+def test_velocity_verlet_energy_error_is_second_order():
+    e1 = _energy_error(0.02)
+    e2 = _energy_error(0.01)
+    assert e1 < 1e-2
+    assert 3.0 < e1 / e2 < 5.5, (e1, e2)
+
+
+@pytest.mark.parametrize("kBT", [1.0, 0.5])
+def test_fluctuation_dissipation_holds_temperature(kBT):
+    w = inputs.bulk(6.0, seed=3, kBT=kBT)
+    gamma = 4.5
+    sigma = math.sqrt(2.0 * gamma * kBT)  # Eq. 8
+    p = oracle.Params(box=w.box, a_ff=25.0, gamma=gamma, sigma=sigma, kBT=kBT, dt=0.01,
+                      lam=0.65, seed=11)
+    s = oracle.init_forces(_state(w), p)
+    temps = []
+    # the random start stores excess conservative energy; let the thermostat
+    # remove it (about 5 time units) before sampling
+    for k in range(2000):
+        s = oracle.step(s, p, _field(w))
+        if k >= 600:
+            v = s.vel
+            temps.append(((v - v.mean(0)) ** 2).sum() / (3 * (len(v) - 1)))
+    T = float(np.mean(temps))
+    assert abs(T / kBT - 1.0) < 0.03, T
+
+
+def test_interpolation_nodes_and_affine_fields():
+    h = 0.25
+    nx, ny, nz = 12, 16, 20
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    grid = (0.5 * i * h - 0.25 * j * h + 0.125 * k * h + 0.1).astype(np.float32)
+    f = oracle.Field(grid, h)
+    rng = np.random.default_rng(0)
+    nodes = np.stack([rng.integers(0, nx, 20), rng.integers(0, ny, 20), rng.integers(0, nz, 20)], 1)
+    vals = oracle.phi_at(f, nodes * h)
+    np.testing.assert_array_equal(vals, grid[nodes[:, 2], nodes[:, 1], nodes[:, 0]].astype(np.float64))
+    # interior points (no periodic wrap between the corner nodes)
+    pts = rng.uniform(0, 1, (50, 3)) * (np.array([nx, ny, nz]) - 1) * h
+    expect = 0.5 * pts[:, 0] - 0.25 * pts[:, 1] + 0.125 * pts[:, 2] + 0.1
+    np.testing.assert_allclose(oracle.phi_at(f, pts), expect, rtol=0, atol=2e-6)
+    # periodicity
+    L = np.array([nx, ny, nz]) * h
+    np.testing.assert_allclose(oracle.phi_at(f, pts + L), oracle.phi_at(f, pts), atol=1e-12)
+    np.testing.assert_allclose(oracle.phi_at(f, pts - 2 * L), oracle.phi_at(f, pts), atol=1e-12)
+
+
+def _lone_particle(w, r0, v0):
+    """One fluid particle in an otherwise empty copy of workload w."""
+    pos = np.array([r0], np.float64)
+    vel = np.array([v0], np.float64)
+    return oracle.State(pos, vel, np.zeros((1, 3)), np.array([0], np.int32), np.zeros(1, np.uint8))
+
+
+def test_bounce_back_lands_on_mirror_point_of_planar_wall():
+    w = inputs.channel(3.0, 3.0, 3.0, seed=0)
+    f = _field(w)
+    p = oracle.Params(box=w.box, a_ff=0.0, gamma=0.0, sigma=0.0, dt=0.01)
+    r0 = np.array([1.1, 1.3, 0.03])
+    v0 = np.array([1.0, -2.0, -4.0])
+    s = oracle.init_forces(_lone_particle(w, r0, v0), p)
+    s1, refl = oracle.step(s, p, f, return_reflected=True)
+    assert refl[0] and s1.stats["reflections"] == 1 and s1.stats["fallbacks"] == 0
+    r1 = r0 + v0 * p.dt                  # would-be position, z = -0.01 (in the solid)
+    # mirror of z = -0.01 about the phi = 0 plane z = 0 (Fig. 4, phi_bb ~ -phi(t+dt))
+    assert abs(s1.pos[0, 2] - 0.01) < 1e-4
+    # the reflected point moves back along the displacement: r_bb = r1 - 2 s dr, 0 < s < 1
+    back = r1 - s1.pos[0]
+    dr = v0 * p.dt
+    sfrac = back[2] / (2 * dr[2])
+    assert 0.0 < sfrac < 1.0
+    np.testing.assert_allclose(back, 2 * sfrac * dr, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(s1.vel[0], -v0)  # bounce-back: all components reversed
+    phi_new = oracle.phi_at(f, r1)[0]
+    phi_bb = oracle.phi_at(f, s1.pos[0])[0]
+    assert phi_new < 0 < phi_bb
+    assert abs(phi_bb + phi_new) < 1e-3 * abs(phi_new)
+
+
+def test_reflected_particle_skips_closing_half_kick():
+    w = inputs.channel(3.0, 3.0, 3.0, seed=0)
+    p = oracle.Params(box=w.box, a_ff=0.0, gamma=0.0, sigma=0.0, dt=0.01, g=(0.5, 0.0, 0.0))
+    pos = np.array([[1.0, 1.0, 0.02], [1.0, 2.0, 1.5]])
+    vel = np.array([[0.2, 0.1, -3.0], [0.2, 0.1, -3.0]])
+    s = oracle.State(pos, vel, np.zeros((2, 3)), np.array([0, 1], np.int32), np.zeros(2, np.uint8))
+    s = oracle.init_forces(s, p)
+    s1, refl = oracle.step(s, p, _field(w), return_reflected=True)
+    assert refl.tolist() == [True, False]
+    np.testing.assert_array_equal(s1.vel[0], -vel[0])
+    np.testing.assert_allclose(s1.vel[1], vel[1] + np.array([0.5, 0, 0]) * p.dt, atol=1e-15)
+
+
+def test_mirror_point_inside_solid_falls_back_to_start():
+    # a fluid film 1.0 < z < 1.2 between two solids, grid spacing 0.05
+    box = (3.0, 3.0, 3.0)
+    h = 0.05
+    n = 60
+    z = np.arange(n) * h
+    d = np.minimum(z - 1.0, 1.2 - z)
+    phi_z = np.tanh(d / (math.sqrt(2) * 0.5)).astype(np.float32)
+    grid = np.broadcast_to(phi_z[:, None, None], (n, n, n)).astype(np.float32).copy()
+    f = oracle.Field(grid, h)
+    p = oracle.Params(box=box, a_ff=0.0, gamma=0.0, sigma=0.0, dt=0.01)
+    r0 = np.array([1.0, 1.0, 1.19])
+    v0 = np.array([0.0, 0.0, 25.0])  # would land at z = 1.44, mirror ~0.96 is solid
+    s = oracle.State(np.array([r0]), np.array([v0]), np.zeros((1, 3)), np.array([0], np.int32),
+                     np.zeros(1, np.uint8))
+    s = oracle.init_forces(s, p)
+    s1 = oracle.step(s, p, f)
+    assert s1.stats == {"reflections": 1, "fallbacks": 1}
+    np.testing.assert_array_equal(s1.pos[0], r0)
+    np.testing.assert_array_equal(s1.vel[0], -v0)
+
+
+def test_no_fluid_particle_ends_a_step_inside_the_solid():
+    w = inputs.channel(5.0, 5.0, 4.0, seed=5)
+    p = oracle.Params(box=w.box, g=(0.05, 0.0, 0.0), seed=2)
+    f = _field(w)
+    s = oracle.init_forces(_state(w), p)
+    solid = w.type != 0
+    spos = s.pos[solid].copy()
+    fluid = ~solid
+    for _ in range(300):
+        s = oracle.step(s, p, f)
+        assert oracle.phi_at(f, s.pos[fluid]).min() >= 0.0
+    assert s.stats["reflections"] > 0
+    np.testing.assert_array_equal(s.pos[solid], spos)
+    assert np.all(s.vel[solid] == 0) and np.all(s.frc[solid] == 0)
+
+
+def test_profile_counts_and_sums_at_bin_centres():
+    nbins, lo, hi = 8, 0.0, 4.0
+    centres = lo + (np.arange(nbins) + 0.5) * (hi - lo) / nbins
+    reps = np.arange(1, nbins + 1)
+    z = np.repeat(centres, reps)
+    pos = np.stack([np.full_like(z, 0.5), np.full_like(z, 0.5), z], 1).astype(np.float32)
+    vel = np.tile([[0.5, -1.0, 2.0]], (len(z), 1))
+    types = np.zeros(len(z), np.uint8)
+    types[0] = 1  # a solid particle is never counted
+    out = oracle.profile(pos, vel, types, 2, nbins, lo, hi)
+    counts = reps.astype(float)
+    counts[0] -= 1
+    np.testing.assert_array_equal(out[:, 0], counts)
+    np.testing.assert_array_equal(out[:, 1], 0.5 * counts)
+    np.testing.assert_array_equal(out[:, 2], -1.0 * counts)
+    np.testing.assert_array_equal(out[:, 3], 2.0 * counts)
+    np.testing.assert_array_equal(out[:, 4], 5.25 * counts)
