@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput of the phase-field no-slip DPD time step on GB300 (particle-steps/s).
+
+A "step" is one full time step of the path: drift + bounce-back reflection +
+cell key (integrate), cell-count scan, counting sort into cell order, pair force
+(conservative + dissipative + Philox random, Eqs. 3-10) + closing half-kick.
+
+Default workload: a plane Poiseuille channel at the paper's DPD parameters
+(rho = 3, a_ff = a_fs = 25, gamma = 4.5, sigma = 3, kBT = 1, dt = 0.01), fluid gap
+64 r_c between phase-field walls, box 80 x 64 x 66 r_c, ~983k fluid + ~31k frozen
+wall particles, body force g_x = 0.01.  Synthetic, seeded inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is device time of K steps replayed from
+CUDA graphs with the state resident in HBM; `e2e` is the same metric through the
+public C ABI from pinned host buffers (load state, K steps, read profile and
+state back); `roofline` is the pair-force kernel's achieved ALU op rate against
+the lane peak; `cpu_baseline` is the FP64 oracle on a bounded slice of the same
+workload on this host's cores.  `--impl reference` times that oracle alone.
+With N > 1 every rank runs its own independent replica (weak scaling; the path
+has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic work of the pair-force kernel (derivation in the design notes).
+# Per candidate (a particle of the 27 surrounding cells): 3 subtractions, 3 x
+# (multiply, round, fused multiply-add) of the minimum image, 3 for r^2, 1 compare.
+OPS_PER_CANDIDATE = 16
+# Per pair inside r_c: Philox4x32-10 (10 rounds x (2 mul-hi + 2 mul-lo + 4 xor +
+# 2 key adds) = 100), uniform + Box-Muller (2 shifts, 2 converts, 2 fma, log,
+# sqrt, cospi, 3 mul = 14), pair force (min image 9, r^2 3, rsqrt + 2, weights 2,
+# direction 3, relative velocity 3 + dot 3, magnitude 4, accumulate 3 = 32).
+OPS_PER_PAIR = 146
+# Algorithmic HBM bytes per particle and step of the whole step (design notes).
+BYTES_PER_PARTICLE_STEP = 380
+SM_COUNT_GB300 = 152
+LANES_PER_SM = 128
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="channel_1m", choices=["channel_1m", "channel_200k"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+WORKLOADS = {
+    # name: (Lx, Ly, gap H, g_x)
+    "channel_1m": (80.0, 64.0, 64.0, 0.01),
+    "channel_200k": (64.0, 32.0, 32.0, 0.01),
+}
+
+
+def _workload(name, seed):
+    from paper_1807_09896_gb300 import inputs
+
+    Lx, Ly, H, gx = WORKLOADS[name]
+    return inputs.channel(Lx, Ly, H, seed=seed), gx
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            hbm = d.get("hbm_gbs") or d.get("hbm_GBs")
+            return float(hbm), "measured", d
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback", {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.uuid = device_uuid
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for f in ("dpd_force.cu", "dpd_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1807_09896_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _force_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, if it still
+    describes the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("source_hash") != _source_hash():
+        return None
+    return d
+
+
+def cpu_oracle_rate(name, budget_s=10.0, min_steps=2, max_steps=None, warmup=0, seed=0):
+    """FP64 oracle throughput on a slice of the workload (same gap and density,
+    smaller Lx x Ly sized to the time budget): `warmup` untimed steps, then timed
+    steps until the budget is used (at least min_steps, at most max_steps)."""
+    import numpy as np
+
+    import oracle
+    from paper_1807_09896_gb300 import inputs
+
+    Lx, Ly, H, gx = WORKLOADS[name]
+    # calibrate on a small slice, then size the slice to the budget
+    probe = inputs.channel(6.0, 6.0, H, seed=seed)
+    p = oracle.Params(box=probe.box, g=(gx, 0, 0), seed=seed)
+    st = oracle.State(probe.pos.astype(np.float64), probe.vel.astype(np.float64),
+                      np.zeros((probe.n, 3)), probe.id.copy(), probe.type.copy())
+    st = oracle.init_forces(st, p)
+    t0 = time.perf_counter()
+    oracle.step(st, p, oracle.Field(probe.phi, probe.h))
+    rate = probe.n_fluid / max(time.perf_counter() - t0, 1e-6)
+    planned = max_steps if max_steps else max(min_steps, 3)
+    per_step = budget_s / planned
+    area = max(16.0, min(Lx * Ly, rate * per_step / (3.0 * H)))
+    side_x = min(Lx, max(4.0, math.floor(math.sqrt(area * Lx / Ly))))
+    side_y = min(Ly, max(4.0, math.floor(area / side_x)))
+    w = inputs.channel(side_x, side_y, H, seed=seed)
+    p = oracle.Params(box=w.box, g=(gx, 0, 0), seed=seed)
+    field = oracle.Field(w.phi, w.h)
+    st = oracle.State(w.pos.astype(np.float64), w.vel.astype(np.float64), np.zeros((w.n, 3)),
+                      w.id.copy(), w.type.copy())
+    st = oracle.init_forces(st, p)
+    for _ in range(warmup):
+        st = oracle.step(st, p, field)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        st = oracle.step(st, p, field)
+        done += 1
+        el = time.perf_counter() - t0
+        if max_steps and done >= max_steps:
+            break
+        if not max_steps and done >= min_steps and el >= budget_s:
+            break
+    return {"value": w.n_fluid * done / el, "unit": "particle-steps/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"channel slice {side_x:g}x{side_y:g} r_c, gap {H:g} ({w.n_fluid} fluid + "
+                      f"{w.n_solid} solid particles) of the {Lx:g}x{Ly:g} workload, {done} FP64 "
+                      f"steps in {el:.1f} s after {warmup} untimed"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each timed step is one oracle step of a slice of the workload sized so that
+    # the W + K steps take about two minutes
+    budget = 120.0 * args.steps / max(1, args.steps + args.warmup)
+    cb = cpu_oracle_rate(args.workload, budget_s=budget, max_steps=max(1, args.steps),
+                         warmup=args.warmup)
+    v = cb["value"]
+    line = {
+        "impl": "reference", "metric": "particle-steps/s", "value": v, "unit": "particle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "note": "FP64 CPU oracle on a slice of the workload"},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_09896_gb300 import _build, dpd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    dev = torch.device("cuda", local)
+    # a real stream (not the legacy default stream) so that the library can capture
+    # CUDA graphs on it and the events below order with its work
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    w, gx = _workload(args.workload, seed=rank)
+    s = dpd.System.from_workload(w, g=(gx, 0.0, 0.0))
+    dpd.dpd_set_stream(s.h, stream)
+    s.set_option("use_graph", 1)
+    s.set_option("graph_steps", 20)
+    s.set_option("seed", rank)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    s.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    launches0 = s.get_option("kernel_launches")
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    launches = int(s.get_option("kernel_launches") - launches0)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.n_fluid * args.steps / (ms / 1e3)
+
+    # phase durations with CUDA events on the library's stream (same launches, no graph)
+    nph = min(args.steps, 50)
+    ph = dpd.dpd_time_phases(s.h, nph)
+    force_ms = ph["force"]
+    cand = 27 * 3.0                 # 27 cells of unit volume at rho = 3
+    pairs = 4.0 / 3.0 * math.pi * 3.0  # neighbours within r_c at rho = 3
+    ops_per_launch = w.n_fluid * (cand * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR)
+    achieved_tops = ops_per_launch / (force_ms / 1e3) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
+    peak_tops = sm_count * LANES_PER_SM * max_mhz * 1e6 / 1e12
+    traffic = _force_traffic()
+    hbm_peak, hbm_src, _ = _peaks()
+    step_gbs = BYTES_PER_PARTICLE_STEP * (w.n_fluid + w.n_solid) * args.steps / (ms / 1e3) / 1e9
+
+    # end to end through the public API from pinned host buffers
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    hp, hv = pin((w.n, 4), torch.float32), pin((w.n, 4), torch.float32)
+    hi, ht = pin((w.n,), torch.int32), pin((w.n,), torch.uint8)
+    hp[:], hv[:], hi[:], ht[:] = w.pos4(), w.vel4(), w.id, w.type
+    op, ov, of = (pin((w.n, 4), torch.float32) for _ in range(3))
+    oi, ot = pin((w.n,), torch.int32), pin((w.n,), torch.uint8)
+    nb = 64
+    prof = pin((nb, 5), torch.float64)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.set_particles(hp, hv, hi, ht)
+    s.step(args.steps)
+    dpd.dpd_velocity_profile(s.h, 2, nb, 0.0, w.gap, mode=1, out=prof)
+    dpd.dpd_get_state(s.h, op, ov, of, oi, ot)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = world * w.n_fluid * args.steps / e2e_s
+    h2d = w.n * (16 + 16 + 4 + 1)
+    d2h = w.n * (16 * 3 + 4 + 1) + nb * 5 * 8
+    st = s.stats()
+    s.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(args.workload, budget_s=10.0)
+
+    if rank == 0:
+        line = {
+            "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"{args.workload}: plane Poiseuille channel, box "
+                            f"{w.box[0]:g}x{w.box[1]:g}x{w.box[2]:g} r_c, gap {w.gap:g}, rho 3, "
+                            f"a 25, gamma 4.5, sigma 3, kBT 1, dt 0.01, g_x {gx}",
+                "n_fluid": w.n_fluid, "n_solid": w.n_solid,
+                "value_counts": "fluid particles only",
+                "l2": "inputs larger than L2: particle state 2 x %.0f MB + phase field %.0f MB" % (
+                    w.n * 64 / 1e6, w.phi.nbytes / 1e6),
+                "graph_steps": 20, "parallelism": f"replicas x{world}",
+            },
+            "roofline": {
+                "kernel": "k_force (pair force + closing half-kick)", "bound": "alu",
+                "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved_tops / peak_tops,
+                "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {max_mhz:g} MHz",
+                "force_ms_per_launch": force_ms, "phase_ms": ph,
+                "traffic": (traffic or {}).get("bytes_per_launch_full"),
+                "step_hbm": {"achieved": step_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": step_gbs / hbm_peak, "peak_source": hbm_src,
+                             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
+            },
+            "e2e": {"value": e2e, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "note": "pinned host state in, K steps, profile + state out, per call"},
+            "gpu_launches": launches,
+            "clocks": ck,
+            "cpu_baseline": cpu,
+            "diagnostics": {"reflections": st[5], "fallbacks": st[6]},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * dpd.h -- C ABI of the GB300 library for one time step of dissipative
+ * particle dynamics (DPD) in a confined geometry with phase-field no-slip
+ * walls (Xu & Meakin, arXiv:1807.09896).
+ *
+ * One handle holds one periodic DPD system: its parameters, its phase field
+ * phi(x) on a grid, and its particles, all resident on the current CUDA
+ * device.  One call of dpd_step advances the system by whole time steps; every
+ * step runs, on the GPU:
+ *   1. drift r' = r + dt v + dt^2/2 F and predicted velocity
+ *      vt = v + lambda dt F of the Groot-Warren modified velocity-Verlet
+ *      scheme the paper uses (Sec. II.A, ref. 35), F = f + g on fluid
+ *      particles (Eq. 1-2; body force g as in Sec. III.A);
+ *   2. bounce-back reflection of every fluid particle whose new position has
+ *      phi < 0, at the sharp phi = 0 surface located with the interpolated
+ *      phase field (Sec. II.C, Eq. 17, Fig. 4);
+ *   3. a cell-list rebuild (counting sort of the particles by cell of edge
+ *      >= r_c; cells hold their particles in ascending id order);
+ *   4. the pair force f_i = sum_j f_ij over all j within r_c = 1
+ *      (Eq. 2), f_ij = f^C + f^D + f^R of Eqs. 3-10 with the random force
+ *      sigma w_R xi_ij / sqrt(dt), xi_ij drawn from Philox4x32-10 keyed by the
+ *      pair and the step;
+ *   5. the closing half-kick v(t+dt) = v + dt/2 (F(t) + F(t+dt)), skipped
+ *      for particles reflected in this step (their velocity is 2 v_wall - v).
+ * Solid (frozen) particles never move and get no force (Sec. II.C).
+ *
+ * Conventions.  DPD units: r_c = 1, particle mass 1.  Arrays of 4 floats per
+ * particle ("pos4", "vel4", "force4") hold x, y, z and one unused pad float.
+ * Particle types: 0 = fluid, 1 = solid.  Particle ids must be a permutation of
+ * 0..n-1; state read back with dpd_get_state is in id order.
+ *
+ * Ownership.  The library copies every input it is given; the caller keeps
+ * its buffers.  Outputs go to caller buffers.  `where` says whether a
+ * caller pointer is host memory (DPD_HOST) or device memory on the handle's
+ * device (DPD_DEVICE).  The library allocates its own device memory in
+ * dpd_set_phase_field and dpd_set_particles (never inside dpd_step).
+ *
+ * Errors.  Every call returns DPD_OK (0) or a negative code below;
+ * dpd_last_error gives a message for the last failure on that handle.  A
+ * handle is used by one host thread at a time.  All GPU work of a handle runs
+ * on one CUDA stream (its own, or the one given to dpd_set_stream).
+ */
+#ifndef DPD_H_
+#define DPD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpd_system dpd_t;
+
+enum {
+  DPD_OK = 0,
+  DPD_EINVAL = -1,   /* bad argument */
+  DPD_ENOMEM = -2,   /* device or host allocation failed */
+  DPD_ECUDA = -3,    /* a CUDA call failed */
+  DPD_ESTATE = -4,   /* call out of order (e.g. dpd_step before dpd_set_particles) */
+  DPD_ELOST = -5,    /* a fluid particle was found at phi < 0 */
+  DPD_EBAND = -6,    /* a drift exceeded the band margin of the reflection test */
+  DPD_ETIMEOUT = -7, /* reserved: a bounded device wait gave up */
+  DPD_ENAN = -8,     /* a non-finite position, velocity or force appeared */
+  DPD_EOVERFLOW = -9 /* a size limit was exceeded (e.g. a cell holds too many particles) */
+};
+
+enum { DPD_HOST = 0, DPD_DEVICE = 1 };
+
+/* Create a system on the current CUDA device.
+ * box[3]      periodic box edges (each >= 3 r_c; cells have edge L / floor(L) >= 1).
+ * rho         nominal number density, used to report densities in profiles.
+ * a_ij[4]     conservative amplitudes a_ff, a_fs, a_sf, a_ss (Eq. 4); only a_ff and
+ *             a_fs enter (solid-solid pairs are never evaluated, a_sf = a_fs).
+ * gamma       dissipative coefficient (Eq. 6).
+ * sigma       random-force coefficient (Eq. 7); Eq. 8 asks sigma^2 = 2 gamma kBT,
+ *             which the library does not enforce.
+ * kBT         temperature (used for reporting only).
+ * dt          time step.
+ * body_force  acceleration g added to the force on every fluid particle.
+ * Options (dpd_set_option) start at: lambda 0.65, band_margin 0.5,
+ * reflect_variant 0, seed 0, system 0, v_wall 0, sample_every 0. */
+int dpd_create(dpd_t** h, const double box[3], double rho, const double a_ij[4], double gamma,
+               double sigma, double kBT, double dt, const double body_force[3]);
+
+/* Set the phase field phi (Sec. II.B): dims[0] x dims[1] x dims[2] float32 node
+ * values, x fastest, node (i, j, k) at (i, j, k) * spacing, periodic; dims[a] *
+ * spacing must equal box[a].  phi > 0 is fluid, phi < 0 solid, phi = 0 the sharp
+ * surface.  The grid is host memory.  Without a phase field phi = +1 everywhere
+ * (no reflection).  Must precede dpd_set_particles. */
+int dpd_set_phase_field(dpd_t* h, const float* grid, const int dims[3], double spacing);
+
+/* Load n particles (any order): pos4 positions (wrapped into the box), vel4
+ * velocities, id a permutation of 0..n-1, type 0 fluid / 1 solid.  Computes the
+ * pair force f(0) at the given state (predicted velocity = v).  Solid
+ * velocities are ignored (frozen at v_wall).  Fails with DPD_ELOST if a fluid
+ * particle sits at phi < 0.  The step counter is kept (see option "step"). */
+int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, const int* id,
+                      const uint8_t* type, int where);
+
+/* Advance nsteps >= 0 time steps.  The device status word is read once at the
+ * end; a non-zero status returns DPD_EBAND / DPD_ENAN / DPD_ELOST /
+ * DPD_EOVERFLOW and stays set until the next dpd_set_particles. */
+int dpd_step(dpd_t* h, int nsteps);
+
+/* Phases of one time step, in launch order, as timed by dpd_time_phases. */
+enum {
+  DPD_PHASE_INTEGRATE = 0, /* counter bump + drift, reflection, cell key and count */
+  DPD_PHASE_SCAN = 1,      /* exclusive scan of the cell counts */
+  DPD_PHASE_SORT = 2,      /* scatter, per-cell id order, gather into cell order */
+  DPD_PHASE_FORCE = 3,     /* pair force (Eqs. 3-10) + closing half-kick */
+  DPD_NPHASES = 4
+};
+
+/* Advance nsteps > 0 time steps exactly as dpd_step does, but launched one by one
+ * (no graph) with CUDA events between the phases of every step on the handle's
+ * stream; ms[DPD_NPHASES] receives each phase's mean duration per step in
+ * milliseconds.  Same results and error codes as dpd_step. */
+int dpd_time_phases(dpd_t* h, int nsteps, double* ms);
+
+/* Copy the state in id order: pos4 / vel4 / force4 (n x 4 floats; the force is
+ * the pair force f without the body force; solid particles have f = 0), id
+ * (n ints, equal to 0..n-1) and type (n bytes).  Any output pointer may be
+ * NULL.  Synchronises the handle's stream. */
+int dpd_get_state(dpd_t* h, float* pos4, float* vel4, float* force4, int* id, uint8_t* type,
+                  int where);
+
+/* Velocity profile of the fluid (Sec. III.A): nbins bins of [lo, hi) along axis
+ * (0, 1, 2).  Per bin the library accumulates, in FP64, five sums over samples
+ * and particles: {count, sum vx, sum vy, sum vz, sum |v|^2}.  mode: 0 = add one
+ * sample of the current state and read; 1 = reset the accumulators (and bin
+ * layout), add one sample, read; 2 = read only; 3 = reset only.  out is host
+ * memory of nbins x 5 doubles (may be NULL for mode 3).  dpd_step also adds a
+ * sample every `sample_every` steps (option) with the current bin layout. */
+int dpd_velocity_profile(dpd_t* h, int axis, int nbins, double lo, double hi, double* out,
+                         int mode);
+
+/* Whole-system diagnostics, FP64: out[0..2] total fluid momentum, out[3] sum
+ * |v|^2 over fluid, out[4] fluid count, out[5] reflections so far, out[6]
+ * fallbacks so far (reflected point still at phi < 0, particle kept at r(t)),
+ * out[7] steps taken (the step counter). */
+int dpd_get_stats(dpd_t* h, double out[8]);
+
+/* Set or read a named option: "lambda", "band_margin", "reflect_variant" (0:
+ * displacement of the step, 1: v(t) dt as printed in Eq. 17), "seed" (integer
+ * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "sample_every",
+ * "step" (the step counter, part of the noise counter), "use_graph" (1: replay
+ * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
+ * default 20).  Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
+ * enqueued by stepping calls so far), "kernels_per_step". */
+int dpd_set_option(dpd_t* h, const char* key, double value);
+int dpd_get_option(dpd_t* h, const char* key, double* value);
+
+/* Particle counts currently loaded. */
+int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
+
+/* Run the handle's work on `stream` (a cudaStream_t; NULL selects the handle's
+ * own stream). */
+int dpd_set_stream(dpd_t* h, void* stream);
+
+/* Free every resource of the handle.  NULL is accepted. */
+int dpd_destroy(dpd_t* h);
+
+/* Message of the last failure on h (or of the last failed dpd_create when h is
+ * NULL).  Never NULL; the string lives until the next call on h. */
+const char* dpd_last_error(const dpd_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPD_H_ */

@@ -64,6 +64,12 @@ def lib() -> ctypes.CDLL:
         L.or_forces.argtypes = [ctypes.c_int, f64p, f64p, i32p, u8p, f64p, ctypes.c_uint32,
                                 ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, f64p]
         L.or_forces.restype = ctypes.c_int
+        L.or_forces_sel.argtypes = [ctypes.c_int, f64p, f64p, i32p, u8p, f64p, ctypes.c_uint32,
+                                    ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                    i32p, f64p, f64p]
+        L.or_forces_sel.restype = ctypes.c_int
+        L.or_phi_many.argtypes = [f32p, i32p, ctypes.c_double, ctypes.c_long, f64p, f64p]
+        L.or_phi_many.restype = None
         L.or_step.argtypes = [ctypes.c_int, f64p, f64p, f64p, i32p, u8p, f64p, f32p, i32p,
                               ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                               ctypes.c_int, u8p, i64p]
@@ -187,6 +193,29 @@ def forces(pos, vt, ids, types, p: Params, step: int, method: int = 1) -> np.nda
     if rc != 0:
         raise RuntimeError(f"or_forces failed ({rc})")
     return f
+
+
+def forces_sel(pos, vt, ids, types, p: Params, step: int, sel, method: int = 1):
+    """Pair force (Eq. 2) on the particles listed in `sel` only, and for each of
+    them sum_j |f_ij| (the scale a force error is judged against)."""
+    pos = _c(pos, np.float64)
+    sel = _c(sel, np.int32)
+    f = np.zeros((len(sel), 3), np.float64)
+    fabs = np.zeros(len(sel), np.float64)
+    rc = lib().or_forces_sel(len(pos), pos.reshape(-1), _c(vt, np.float64).reshape(-1),
+                             _c(ids, np.int32), _c(types, np.uint8), p.flat(), step, p.sys, p.seed,
+                             method, len(sel), sel, f.reshape(-1), fabs)
+    if rc != 0:
+        raise RuntimeError(f"or_forces_sel failed ({rc})")
+    return f, fabs
+
+
+def phi_many(f: Field, pts) -> np.ndarray:
+    """Phase field at many points (n, 3), computed in C."""
+    pts = _c(np.atleast_2d(pts), np.float64)
+    out = np.zeros(len(pts), np.float64)
+    lib().or_phi_many(_c(f.grid, np.float32).reshape(-1), f.dims, f.h, len(pts), pts.reshape(-1), out)
+    return out
 
 
 def init_forces(s: State, p: Params, method: int = 1) -> State:

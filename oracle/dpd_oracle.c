@@ -299,9 +299,22 @@ static void pair_force(const double* P, const double d[3], double r, const doubl
 /* The total pair force on every fluid particle (Eq. 2), evaluated with the
  * predicted velocities vt; solid particles get zero (reading R9).  The
  * noise counter uses `step`.  method 0 = all pairs, 1 = cell list. */
+int or_forces_sel(int n, const double* pos, const double* vt, const int* id,
+                  const uint8_t* type, const double* P, uint32_t step, uint32_t sys,
+                  uint64_t seed, int method, int nsel, const int* sel, double* f, double* fabs_sum);
+
 int or_forces(int n, const double* pos, const double* vt, const int* id, const uint8_t* type,
               const double* P, uint32_t step, uint32_t sys, uint64_t seed, int method,
               double* f) {
+  return or_forces_sel(n, pos, vt, id, type, P, step, sys, seed, method, -1, NULL, f, NULL);
+}
+
+/* As or_forces, for the particles listed in sel (nsel of them; nsel < 0 means
+ * all) -- f and fabs_sum are indexed like sel.  fabs_sum (may be NULL)
+ * receives sum_j |f_ij|, the scale against which a force error is judged. */
+int or_forces_sel(int n, const double* pos, const double* vt, const int* id,
+                  const uint8_t* type, const double* P, uint32_t step, uint32_t sys,
+                  uint64_t seed, int method, int nsel, const int* sel, double* f, double* fabs_sum) {
   const double L[3] = {P[P_LX], P[P_LY], P[P_LZ]};
   cells_t C;
   memset(&C, 0, sizeof C);
@@ -311,10 +324,14 @@ int or_forces(int n, const double* pos, const double* vt, const int* id, const u
   {
     int* nb = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     if (!nb) fail = 1;
+    const int nout = nsel < 0 ? n : nsel;
 #pragma omp for schedule(static)
-    for (int i = 0; i < n; ++i) {
-      f[3 * i] = f[3 * i + 1] = f[3 * i + 2] = 0.0;
-      if (!nb || type[i] != 0) continue;
+    for (int q0 = 0; q0 < nout; ++q0) {
+      const int i = nsel < 0 ? q0 : sel[q0];
+      double* fo = &f[3 * q0];
+      fo[0] = fo[1] = fo[2] = 0.0;
+      if (fabs_sum) fabs_sum[q0] = 0.0;
+      if (!nb || i < 0 || i >= n || type[i] != 0) continue;
       int k = neighbours_of(i, n, pos, L, method, &C, nb, n);
       for (int q = 0; q < k; ++q) {
         int j = nb[q];
@@ -332,9 +349,10 @@ int or_forces(int n, const double* pos, const double* vt, const int* id, const u
         double xi = or_xi((uint32_t)id[i], (uint32_t)id[j], step, sys, seed);
         double fij[3];
         pair_force(P, d, r, vij, type[i], type[j], xi, fij);
-        f[3 * i] += fij[0];
-        f[3 * i + 1] += fij[1];
-        f[3 * i + 2] += fij[2];
+        fo[0] += fij[0];
+        fo[1] += fij[1];
+        fo[2] += fij[2];
+        if (fabs_sum) fabs_sum[q0] += sqrt(fij[0] * fij[0] + fij[1] * fij[1] + fij[2] * fij[2]);
       }
     }
     free(nb);
@@ -469,6 +487,12 @@ void or_profile(int n, const float* pos4, const double* vel, const uint8_t* type
     out[5 * b + 3] += vz;
     out[5 * b + 4] += vx * vx + vy * vy + vz * vz;
   }
+}
+
+/* Phase field at many points (see or_phi_at). */
+void or_phi_many(const float* grid, const int dims[3], double h, long m, const double* pts,
+                 double* out) {
+  for (long k = 0; k < m; ++k) out[k] = or_phi_at(grid, dims, h, pts[3 * k], pts[3 * k + 1], pts[3 * k + 2]);
 }
 
 int or_num_threads(void) {

@@ -1,0 +1,163 @@
+// dpd_common.cuh -- device-side types and helpers shared by the kernels of the
+// GB300 DPD library (phase-field no-slip walls, Xu & Meakin, arXiv:1807.09896).
+//
+// Particle data live as structure-of-arrays of float4 in cell order:
+//   pos  {x, y, z, tag}   tag = bit pattern of (id | solid << 31)
+//   vt   {vtx, vty, vtz, reflected flag}   predicted velocity of the step
+//   vel  {vx, vy, vz, 0}  velocity v(t)
+//   frc  {fx, fy, fz, 0}  pair force f(t) (body force not included)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpd {
+
+constexpr uint32_t kSolidBit = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7fffffffu;
+
+// Device status bits (read by dpd_step once per call).
+enum : uint32_t {
+  ST_BAND = 1u,      // a drift exceeded the band margin
+  ST_NAN = 2u,       // non-finite value
+  ST_LOST = 4u,      // fluid particle at phi < 0
+  ST_OVERFLOW = 8u,  // a cell exceeded the per-cell sort capacity
+  ST_BADID = 16u,    // ids are not a permutation of 0..n-1
+};
+
+struct DevCounters {
+  uint32_t status;
+  uint32_t step;                 // noise counter of the most recent force evaluation
+  unsigned long long reflections;
+  unsigned long long fallbacks;
+};
+
+// Everything a step kernel needs, passed by value.
+struct StepParams {
+  float L[3], invL[3], halfL[3];
+  int nc[3];
+  float inv_edge[3];
+  int ncells;
+  float dt, half_dt, half_dt2, lam_dt;
+  float g[3], vw[3];
+  float a_ff, a_fs, gamma, sigma_rsqdt;
+  uint32_t seed_lo, seed_hi, sys;
+  int reflect_variant;
+  float margin;
+  const float* phi;   // phase-field nodes, x fastest (nullptr: phi = +1)
+  int pd[3];
+  float inv_h;
+  const uint8_t* band;  // per cell: 1 if a particle starting there may reach phi < 0
+};
+
+struct Arrays {
+  float4* pos;
+  float4* vt;
+  float4* vel;
+  float4* frc;
+};
+
+struct CellList {
+  uint32_t* key;    // cell of each particle (current order)
+  uint32_t* rank;   // arrival slot inside its cell (atomic order)
+  uint32_t* count;  // particles per cell (zeroed by the scan)
+  uint32_t* start;  // exclusive prefix of count, ncells + 1 entries
+  uint32_t* perm;   // new position -> old position
+  uint32_t* blocksum;
+};
+
+__device__ __forceinline__ uint32_t tag_of(float w) { return __float_as_uint(w); }
+__device__ __forceinline__ bool is_solid(float w) { return (tag_of(w) & kSolidBit) != 0u; }
+__device__ __forceinline__ uint32_t id_of(float w) { return tag_of(w) & kIdMask; }
+
+__device__ __forceinline__ int cell_coord(float x, float inv_edge, int nc) {
+  int c = __float2int_rd(x * inv_edge);
+  return min(max(c, 0), nc - 1);
+}
+
+__device__ __forceinline__ int cell_of(const StepParams& P, float x, float y, float z) {
+  int cx = cell_coord(x, P.inv_edge[0], P.nc[0]);
+  int cy = cell_coord(y, P.inv_edge[1], P.nc[1]);
+  int cz = cell_coord(z, P.inv_edge[2], P.nc[2]);
+  return (cz * P.nc[1] + cy) * P.nc[0] + cx;
+}
+
+__device__ __forceinline__ int wrap_node(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+// Particle phase field: trilinear interpolation of the periodic node grid at an
+// arbitrary (possibly unwrapped) point (Sec. II.C, 3-D form of the paper's
+// linear interpolation).  The point may be given as an unevaluated sum x + lx
+// (a binary32 value and its rounding error); the fractional offsets inside the
+// grid cell are then formed from the exact sum, so a point a few ulp(L) from a
+// node plane keeps its full relative accuracy.
+__device__ __forceinline__ float phi_at(const StepParams& P, float x, float y, float z,
+                                        float lx = 0.0f, float ly = 0.0f, float lz = 0.0f) {
+  if (P.phi == nullptr) return 1.0f;
+  const float fx = floorf(x * P.inv_h), fy = floorf(y * P.inv_h), fz = floorf(z * P.inv_h);
+  const float tx = fmaf(x, P.inv_h, -fx) + lx * P.inv_h;
+  const float ty = fmaf(y, P.inv_h, -fy) + ly * P.inv_h;
+  const float tz = fmaf(z, P.inv_h, -fz) + lz * P.inv_h;
+  const int ix0 = wrap_node(__float2int_rd(fx), P.pd[0]), ix1 = wrap_node(__float2int_rd(fx) + 1, P.pd[0]);
+  const int iy0 = wrap_node(__float2int_rd(fy), P.pd[1]), iy1 = wrap_node(__float2int_rd(fy) + 1, P.pd[1]);
+  const int iz0 = wrap_node(__float2int_rd(fz), P.pd[2]), iz1 = wrap_node(__float2int_rd(fz) + 1, P.pd[2]);
+  const int sy_ = P.pd[0];
+  const long sz_ = (long)P.pd[0] * P.pd[1];
+  const float* g = P.phi;
+  const float c000 = __ldg(g + iz0 * sz_ + iy0 * sy_ + ix0), c100 = __ldg(g + iz0 * sz_ + iy0 * sy_ + ix1);
+  const float c010 = __ldg(g + iz0 * sz_ + iy1 * sy_ + ix0), c110 = __ldg(g + iz0 * sz_ + iy1 * sy_ + ix1);
+  const float c001 = __ldg(g + iz1 * sz_ + iy0 * sy_ + ix0), c101 = __ldg(g + iz1 * sz_ + iy0 * sy_ + ix1);
+  const float c011 = __ldg(g + iz1 * sz_ + iy1 * sy_ + ix0), c111 = __ldg(g + iz1 * sz_ + iy1 * sy_ + ix1);
+  const float ux = 1.0f - tx, uy = 1.0f - ty, uz = 1.0f - tz;
+  const float c00 = c000 * ux + c100 * tx, c10 = c010 * ux + c110 * tx;
+  const float c01 = c001 * ux + c101 * tx, c11 = c011 * ux + c111 * tx;
+  const float c0 = c00 * uy + c10 * ty, c1 = c01 * uy + c11 * ty;
+  return c0 * uz + c1 * tz;
+}
+
+// s + err = a + b exactly (Knuth's TwoSum; no multiplications, so no contraction).
+__device__ __forceinline__ float two_sum(float a, float b, float* err) {
+  const float s = a + b;
+  const float bb = s - a;
+  *err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// Pair noise xi_ij of Eq. 7.  Philox4x32-10 (Salmon et al., SC'11) of the
+// counter (min id, max id, step, system) under the key (seed_lo, seed_hi); the
+// first two output words become two uniforms u = ((w >> 9) + 1/2) 2^-23, exact in
+// binary32, and the Box-Muller transform gives xi = sqrt(-2 ln u0) cos(2 pi u1).
+__device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t step, uint32_t sys,
+                                            uint32_t k0, uint32_t k1) {
+  uint32_t c0 = min(ida, idb), c1 = max(ida, idb), c2 = step, c3 = sys;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  const float u0 = (__uint2float_rn(c0 >> 9) + 0.5f) * 0x1p-23f;
+  const float u1 = (__uint2float_rn(c1 >> 9) + 0.5f) * 0x1p-23f;
+  return sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+}
+
+// Minimum-image separation xi - xj of two coordinates in [0, L).  When the pair
+// straddles the periodic seam the operand near L is shifted by -L first; that
+// shift is exact (Sterbenz: the operand lies in [L/2, L)), so the separation is
+// rounded once, at its own magnitude (below r_c), instead of at the magnitude of
+// L.  Swapping i and j negates the result exactly.
+__device__ __forceinline__ float min_image(float xi, float xj, float L, float halfL) {
+  const float d = xi - xj;
+  if (d > halfL) return (xi - L) - xj;
+  if (d < -halfL) return xi - (xj - L);
+  return d;
+}
+
+}  // namespace dpd

@@ -1,0 +1,483 @@
+// dpd_kernels.cu -- the streaming kernels of one DPD time step: drift and
+// bounce-back reflection, cell-list counting sort, profile and diagnostic
+// reductions, and set-up helpers (Xu & Meakin, arXiv:1807.09896).
+//
+// All of these are bound by HBM bandwidth: each touches every particle once
+// with coalesced float4 loads and stores in cell order.
+#include "dpd_common.cuh"
+#include "dpd_launch.h"
+
+namespace dpd {
+
+// ---------------------------------------------------------------------------
+// Step kernel 1: drift, predicted velocity, reflection, cell key.
+//
+// Groot-Warren modified velocity-Verlet (Sec. II.A, ref. 35), F = f + g:
+//   dr = dt v + dt^2/2 F,  r' = r + dr,  vt = v + lambda dt F.
+// Bounce-back (Sec. II.C, Eq. 17, Fig. 4): if phi(r') < 0 the particle is put
+// at r' - 2 s dr with s = atanh(-phi(r')) / (atanh(-phi(r')) + atanh(phi(r))),
+// its velocity becomes 2 v_wall - v(t) (also used as vt), and it is flagged so
+// that the closing half-kick is skipped.  If the reflected point still has
+// phi < 0 the particle stays at r(t).  The test runs only for particles whose
+// starting cell is flagged in the band mask (Sec. II.C: bulk particles far from
+// phi = 0 need no test); the band is conservative for drifts up to `margin`,
+// which is checked.
+// Then the position is wrapped into the box, its cell found, and the particle
+// counted into that cell with one atomic that also gives its arrival slot.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float clamp_phi(float p) {
+  return fminf(fmaxf(p, -0.999999f), 0.999999f);
+}
+
+__device__ __forceinline__ float wrap_coord(float x, float L) {
+  if (x < 0.0f) {
+    x += L;
+    if (x >= L) x = 0.0f;
+  } else if (x >= L) {
+    x -= L;
+    if (x >= L) x = 0.0f;
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(256) k_integrate(StepParams P, Arrays A, CellList C, int n,
+                                                   DevCounters* ctr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 p = A.pos[i];
+  if (!is_solid(p.w)) {
+    const float4 v = A.vel[i];
+    const float4 f = A.frc[i];
+    const float Fx = f.x + P.g[0], Fy = f.y + P.g[1], Fz = f.z + P.g[2];
+    const float dx = fmaf(P.half_dt2, Fx, P.dt * v.x);
+    const float dy = fmaf(P.half_dt2, Fy, P.dt * v.y);
+    const float dz = fmaf(P.half_dt2, Fz, P.dt * v.z);
+    // r' = r + dr, kept as the unevaluated sum x + lx for the phase-field lookup
+    float lx, ly, lz;
+    float x = two_sum(p.x, dx, &lx), y = two_sum(p.y, dy, &ly), z = two_sum(p.z, dz, &lz);
+    float4 vt = make_float4(fmaf(P.lam_dt, Fx, v.x), fmaf(P.lam_dt, Fy, v.y),
+                            fmaf(P.lam_dt, Fz, v.z), 0.0f);
+    if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) > P.margin) atomicOr(&ctr->status, ST_BAND);
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(&ctr->status, ST_NAN);
+    if (P.band != nullptr && P.band[cell_of(P, p.x, p.y, p.z)]) {
+      const float phi_new = phi_at(P, x, y, z, lx, ly, lz);
+      if (phi_new < 0.0f) {
+        const float phi_old = fmaxf(phi_at(P, p.x, p.y, p.z), 0.0f);
+        const float Ad = atanhf(-clamp_phi(phi_new));
+        const float Bd = atanhf(clamp_phi(phi_old));
+        const float s2 = 2.0f * (Ad / (Ad + Bd));
+        float ex = dx, ey = dy, ez = dz;
+        if (P.reflect_variant == 1) {
+          ex = (v.x - P.vw[0]) * P.dt;
+          ey = (v.y - P.vw[1]) * P.dt;
+          ez = (v.z - P.vw[2]) * P.dt;
+        }
+        // r_bb = r' - 2 s e = r + (dr - 2 s e): one rounding, from the exact r
+        const float qx = fmaf(-s2, ex, dx), qy = fmaf(-s2, ey, dy), qz = fmaf(-s2, ez, dz);
+        float mx, my, mz;
+        float bx = two_sum(p.x, qx, &mx), by = two_sum(p.y, qy, &my), bz = two_sum(p.z, qz, &mz);
+        if (phi_at(P, bx, by, bz, mx, my, mz) < 0.0f) {
+          bx = p.x; by = p.y; bz = p.z;
+          atomicAdd(&ctr->fallbacks, 1ull);
+        }
+        x = bx; y = by; z = bz;
+        const float4 vb = make_float4(2.0f * P.vw[0] - v.x, 2.0f * P.vw[1] - v.y,
+                                      2.0f * P.vw[2] - v.z, 0.0f);
+        A.vel[i] = vb;
+        vt = make_float4(vb.x, vb.y, vb.z, 1.0f);
+        atomicAdd(&ctr->reflections, 1ull);
+      }
+    }
+    p.x = wrap_coord(x, P.L[0]);
+    p.y = wrap_coord(y, P.L[1]);
+    p.z = wrap_coord(z, P.L[2]);
+    A.pos[i] = p;
+    A.vt[i] = vt;
+  }
+  const int c = cell_of(P, p.x, p.y, p.z);
+  C.key[i] = (uint32_t)c;
+  C.rank[i] = atomicAdd(&C.count[c], 1u);
+}
+
+// Cell key only (set-up: particles loaded, nothing moves).
+__global__ void k_key(StepParams P, Arrays A, CellList C, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = A.pos[i];
+  const int c = cell_of(P, p.x, p.y, p.z);
+  C.key[i] = (uint32_t)c;
+  C.rank[i] = atomicAdd(&C.count[c], 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the per-cell counts, in three passes (block sums, scan of
+// the block sums, scan inside each block with the block offset).  No block
+// waits on another, so nothing can spin.  Warp scans use __shfl_up_sync.
+// The last pass also zeroes the counts for the next step.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
+constexpr int kScanChunk = kScanThreads * kScanPerThread;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total in *total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+    t = warp_incl_scan(t);
+    if (lane < kScanThreads / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t base = warp > 0 ? warp_tot[warp - 1] : 0u;
+  *total = warp_tot[kScanThreads / 32 - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* count, int m,
+                                                              uint32_t* blocksum) {
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPerThread;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k)
+    if (base + k < m) s += count[base + k];
+  uint32_t tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+}
+
+// One block scans the block sums in place (exclusive), looping over chunks.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* blocksum, int nb) {
+  uint32_t carry = 0;
+  for (int off = 0; off < nb; off += kScanThreads) {
+    const int j = off + threadIdx.x;
+    const uint32_t v = j < nb ? blocksum[j] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, &tot);
+    if (j < nb) blocksum[j] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* count, int m,
+                                                            const uint32_t* blocksum,
+                                                            uint32_t* start, uint32_t n_total) {
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPerThread;
+  uint32_t v[kScanPerThread];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    v[k] = (base + k < m) ? count[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t run = blocksum[blockIdx.x] + block_excl_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    if (base + k < m) {
+      start[base + k] = run;
+      count[base + k] = 0u;
+    }
+    run += v[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[m] = n_total;
+}
+
+// ---------------------------------------------------------------------------
+// Counting-sort scatter, per-cell id order, and the gather that reorders the
+// particle arrays into cell order.
+// ---------------------------------------------------------------------------
+__global__ void k_scatter(CellList C, int n, DevCounters* ctr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t d = C.start[C.key[i]] + C.rank[i];
+  if (d < (uint32_t)n)
+    C.perm[d] = (uint32_t)i;
+  else
+    atomicOr(&ctr->status, ST_OVERFLOW);  // inconsistent counts: never write out of range
+}
+
+// One thread per cell: put the cell's entries of perm in ascending particle id
+// order (insertion sort; cells hold a handful of particles).  This makes the
+// order of every later floating-point sum independent of atomic timing.
+constexpr int kCellSortCap = 48;
+
+__global__ void k_cell_sort(CellList C, const float4* pos, int n, int ncells, DevCounters* ctr) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const uint32_t b = C.start[c], e = C.start[c + 1];
+  const int m = (int)(e - b);
+  if (m <= 1) return;
+  if (m > kCellSortCap) {
+    atomicOr(&ctr->status, ST_OVERFLOW);
+    return;
+  }
+  uint32_t idx[kCellSortCap];
+  uint32_t key[kCellSortCap];
+  for (int k = 0; k < m; ++k) {
+    const uint32_t j = min(C.perm[b + k], (uint32_t)(n - 1));
+    const uint32_t id = id_of(pos[j].w);
+    int q = k;
+    while (q > 0 && key[q - 1] > id) {
+      key[q] = key[q - 1];
+      idx[q] = idx[q - 1];
+      --q;
+    }
+    key[q] = id;
+    idx[q] = j;
+  }
+  for (int k = 0; k < m; ++k) C.perm[b + k] = idx[k];
+}
+
+__global__ void __launch_bounds__(256) k_gather(Arrays src, Arrays dst, const uint32_t* perm, int n) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const uint32_t s = min(perm[d], (uint32_t)(n - 1));
+  dst.pos[d] = src.pos[s];
+  dst.vt[d] = src.vt[s];
+  dst.vel[d] = src.vel[s];
+  dst.frc[d] = src.frc[s];
+}
+
+// ---------------------------------------------------------------------------
+// Profile sums (Sec. III.A) and whole-system diagnostics, FP64.
+// Warps reduce with shuffles: lanes that share a bin add their values with a
+// butterfly, and one lane per warp and bin issues the FP64 atomics.  The bin
+// index is decided in binary32: b = floor((x - lo) * (nbins / (hi - lo))).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_profile(const float4* pos, const float4* vel, int n, int axis,
+                                                 int nbins, float lo, float inv_w, double* acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  bool pending = false;
+  int bin = 0;
+  double vx = 0, vy = 0, vz = 0;
+  if (i < n) {
+    const float4 p = pos[i];
+    if (!is_solid(p.w)) {
+      const float x = axis == 0 ? p.x : (axis == 1 ? p.y : p.z);
+      const float u = __fmul_rn(__fsub_rn(x, lo), inv_w);
+      const float fb = floorf(u);
+      if (fb >= 0.0f && fb < (float)nbins) {
+        bin = (int)fb;
+        pending = true;
+        const float4 v = vel[i];
+        vx = v.x; vy = v.y; vz = v.z;
+      }
+    }
+  }
+  unsigned mask = __ballot_sync(0xffffffffu, pending);
+  while (mask) {
+    const int leader = __ffs(mask) - 1;
+    const int b0 = __shfl_sync(0xffffffffu, bin, leader);
+    const bool mine = pending && bin == b0;
+    const double c = warp_sum(mine ? 1.0 : 0.0);
+    const double sx = warp_sum(mine ? vx : 0.0);
+    const double sy = warp_sum(mine ? vy : 0.0);
+    const double sz = warp_sum(mine ? vz : 0.0);
+    const double s2 = warp_sum(mine ? vx * vx + vy * vy + vz * vz : 0.0);
+    if (lane == leader) {
+      double* a = acc + 5 * b0;
+      atomicAdd(a + 0, c);
+      atomicAdd(a + 1, sx);
+      atomicAdd(a + 2, sy);
+      atomicAdd(a + 3, sz);
+      atomicAdd(a + 4, s2);
+    }
+    if (mine) pending = false;
+    mask = __ballot_sync(0xffffffffu, pending);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stats(const float4* pos, const float4* vel, int n, double* acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double vx = 0, vy = 0, vz = 0, c = 0;
+  if (i < n) {
+    const float4 p = pos[i];
+    if (!is_solid(p.w)) {
+      const float4 v = vel[i];
+      vx = v.x; vy = v.y; vz = v.z; c = 1.0;
+    }
+  }
+  const double s2 = warp_sum(vx * vx + vy * vy + vz * vz);
+  vx = warp_sum(vx); vy = warp_sum(vy); vz = warp_sum(vz); c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc + 0, vx);
+    atomicAdd(acc + 1, vy);
+    atomicAdd(acc + 2, vz);
+    atomicAdd(acc + 3, s2);
+    atomicAdd(acc + 4, c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up kernels.
+// ---------------------------------------------------------------------------
+// Band mask: a cell is flagged when some point within `margin` of it may have
+// phi < 0.  Trilinear interpolation is a convex combination of its eight corner
+// nodes, so a point can have phi < 0 only if one of the nodes around it is
+// negative; the cell is flagged iff a node in the range covering the cell grown
+// by the margin is negative.
+__global__ void k_band(StepParams P, uint8_t* band) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.ncells) return;
+  const int cx = c % P.nc[0];
+  const int cy = (c / P.nc[0]) % P.nc[1];
+  const int cz = c / (P.nc[0] * P.nc[1]);
+  const int cc[3] = {cx, cy, cz};
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    const float edge = P.L[a] / P.nc[a];
+    lo[a] = (int)floorf((cc[a] * edge - P.margin) * P.inv_h) - 1;
+    hi[a] = (int)floorf(((cc[a] + 1) * edge + P.margin) * P.inv_h) + 2;
+  }
+  bool neg = false;
+  for (int k = lo[2]; k <= hi[2] && !neg; ++k) {
+    const int kz = wrap_node(k, P.pd[2]);
+    for (int j = lo[1]; j <= hi[1] && !neg; ++j) {
+      const int jy = wrap_node(j, P.pd[1]);
+      const float* row = P.phi + ((long)kz * P.pd[1] + jy) * P.pd[0];
+      for (int ii = lo[0]; ii <= hi[0]; ++ii) {
+        if (row[wrap_node(ii, P.pd[0])] < 0.0f) {
+          neg = true;
+          break;
+        }
+      }
+    }
+  }
+  band[c] = neg ? 1 : 0;
+}
+
+// Build the internal arrays from caller input (any order, id a permutation).
+__global__ void k_load(StepParams P, const float4* in_pos, const float4* in_vel, const int* in_id,
+                       const uint8_t* in_type, Arrays A, uint32_t* seen, int n, DevCounters* ctr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int id = in_id[i];
+  if (id < 0 || id >= n || atomicExch(&seen[id], 1u) != 0u) {
+    atomicOr(&ctr->status, ST_BADID);
+    return;
+  }
+  const bool solid = in_type[i] != 0;
+  const float4 q = in_pos[i];
+  float4 p;
+  p.x = wrap_coord(q.x - P.L[0] * floorf(q.x * P.invL[0]), P.L[0]);
+  p.y = wrap_coord(q.y - P.L[1] * floorf(q.y * P.invL[1]), P.L[1]);
+  p.z = wrap_coord(q.z - P.L[2] * floorf(q.z * P.invL[2]), P.L[2]);
+  p.w = __uint_as_float((uint32_t)id | (solid ? kSolidBit : 0u));
+  if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) atomicOr(&ctr->status, ST_NAN);
+  float4 v = in_vel[i];
+  v.w = 0.0f;
+  if (solid) v = make_float4(P.vw[0], P.vw[1], P.vw[2], 0.0f);
+  if (!solid && phi_at(P, p.x, p.y, p.z) < 0.0f) atomicOr(&ctr->status, ST_LOST);
+  A.pos[i] = p;
+  A.vel[i] = solid ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
+  A.vt[i] = v;
+  A.frc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Unsort into id order (outputs may be null).
+__global__ void k_unsort(Arrays A, int n, float4* out_pos, float4* out_vel, float4* out_frc,
+                         int* out_id, uint8_t* out_type) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = A.pos[i];
+  const uint32_t id = id_of(p.w);
+  if (id >= (uint32_t)n) return;
+  if (out_pos) out_pos[id] = make_float4(p.x, p.y, p.z, 0.0f);
+  if (out_vel) {
+    float4 v = A.vel[i];
+    v.w = 0.0f;
+    out_vel[id] = v;
+  }
+  if (out_frc) {
+    float4 f = A.frc[i];
+    f.w = 0.0f;
+    out_frc[id] = f;
+  }
+  if (out_id) out_id[id] = (int)id;
+  if (out_type) out_type[id] = is_solid(p.w) ? 1 : 0;
+}
+
+__global__ void k_bump_step(DevCounters* ctr) { ctr->step += 1u; }
+
+// ---------------------------------------------------------------------------
+// Host launch wrappers.
+// ---------------------------------------------------------------------------
+static inline int blocks(long n, int t) { return (int)((n + t - 1) / t); }
+
+void launch_integrate(const StepParams& P, const Arrays& A, const CellList& C, int n,
+                      DevCounters* ctr, cudaStream_t s) {
+  if (n > 0) k_integrate<<<blocks(n, 256), 256, 0, s>>>(P, A, C, n, ctr);
+}
+
+void launch_key(const StepParams& P, const Arrays& A, const CellList& C, int n, cudaStream_t s) {
+  if (n > 0) k_key<<<blocks(n, 256), 256, 0, s>>>(P, A, C, n);
+}
+
+int scan_blocks(int ncells) { return blocks(ncells, kScanChunk); }
+
+void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s) {
+  const int nb = scan_blocks(ncells);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(C.blocksum, nb);
+  k_scan_down<<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum, C.start, (uint32_t)n);
+}
+
+void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
+                 DevCounters* ctr, cudaStream_t s) {
+  if (n <= 0) return;
+  k_scatter<<<blocks(n, 256), 256, 0, s>>>(C, n, ctr);
+  k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, src.pos, n, ncells, ctr);
+  k_gather<<<blocks(n, 256), 256, 0, s>>>(src, dst, C.perm, n);
+}
+
+void launch_profile(const float4* pos, const float4* vel, int n, int axis, int nbins, float lo,
+                    float inv_w, double* acc, cudaStream_t s) {
+  if (n > 0) k_profile<<<blocks(n, 256), 256, 0, s>>>(pos, vel, n, axis, nbins, lo, inv_w, acc);
+}
+
+void launch_stats(const float4* pos, const float4* vel, int n, double* acc, cudaStream_t s) {
+  if (n > 0) k_stats<<<blocks(n, 256), 256, 0, s>>>(pos, vel, n, acc);
+}
+
+void launch_band(const StepParams& P, uint8_t* band, cudaStream_t s) {
+  k_band<<<blocks(P.ncells, 128), 128, 0, s>>>(P, band);
+}
+
+void launch_load(const StepParams& P, const float4* in_pos, const float4* in_vel, const int* in_id,
+                 const uint8_t* in_type, const Arrays& A, uint32_t* seen, int n, DevCounters* ctr,
+                 cudaStream_t s) {
+  if (n > 0)
+    k_load<<<blocks(n, 256), 256, 0, s>>>(P, in_pos, in_vel, in_id, in_type, A, seen, n, ctr);
+}
+
+void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, float4* out_frc,
+                   int* out_id, uint8_t* out_type, cudaStream_t s) {
+  if (n > 0)
+    k_unsort<<<blocks(n, 256), 256, 0, s>>>(A, n, out_pos, out_vel, out_frc, out_id, out_type);
+}
+
+void launch_bump_step(DevCounters* ctr, cudaStream_t s) { k_bump_step<<<1, 1, 0, s>>>(ctr); }
+
+}  // namespace dpd

@@ -1,0 +1,28 @@
+// dpd_launch.h -- host-side launch wrappers of the DPD kernels (internal).
+#pragma once
+
+#include "dpd_common.cuh"
+
+namespace dpd {
+
+void launch_integrate(const StepParams& P, const Arrays& A, const CellList& C, int n,
+                      DevCounters* ctr, cudaStream_t s);
+void launch_key(const StepParams& P, const Arrays& A, const CellList& C, int n, cudaStream_t s);
+int scan_blocks(int ncells);
+void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s);
+void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
+                 DevCounters* ctr, cudaStream_t s);
+void launch_force(const StepParams& P, const Arrays& A, const uint32_t* start, int n,
+                  DevCounters* ctr, int kick, cudaStream_t s);
+void launch_profile(const float4* pos, const float4* vel, int n, int axis, int nbins, float lo,
+                    float inv_w, double* acc, cudaStream_t s);
+void launch_stats(const float4* pos, const float4* vel, int n, double* acc, cudaStream_t s);
+void launch_band(const StepParams& P, uint8_t* band, cudaStream_t s);
+void launch_load(const StepParams& P, const float4* in_pos, const float4* in_vel, const int* in_id,
+                 const uint8_t* in_type, const Arrays& A, uint32_t* seen, int n, DevCounters* ctr,
+                 cudaStream_t s);
+void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, float4* out_frc,
+                   int* out_id, uint8_t* out_type, cudaStream_t s);
+void launch_bump_step(DevCounters* ctr, cudaStream_t s);
+
+}  // namespace dpd

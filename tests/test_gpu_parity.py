@@ -1,0 +1,247 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Each comparison starts GPU and oracle from the same binary32 state, read back from
+the GPU, and compares one step (drift, reflection, cell list, forces, closing
+kick) particle by particle under the tolerances of tests/parity_helpers.py.
+Sizes run from a 3x3x3 box (the smallest cell grid, every cell on the periodic
+seam) through several thread blocks with a ragged tail up to the benchmark's
+channel of about one million fluid particles.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_09896_gb300 import dpd, inputs
+from parity_helpers import (check_forces, compare_one_step, force_scales, gpu_state,
+                            make_system, params_for)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1807_09896_gb300 import _build
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _build.build()
+
+
+def _field(w):
+    return oracle.Field(w.phi, w.h)
+
+
+def _initial_force_parity(w, p):
+    s = make_system(w, p)
+    pos, vel, frc, types = gpu_state(s)
+    ids = np.arange(len(pos))
+    vt = vel.astype(np.float64)
+    vt[types != 0] = 0.0
+    f_or, fabs = force_scales(pos.astype(np.float64), vt, ids, types, p, 0)
+    err = check_forces(frc, f_or, fabs, types, what="f(0)")
+    # the GPU keeps the input state exactly
+    np.testing.assert_array_equal(pos, w.pos)
+    np.testing.assert_array_equal(vel[types == 0], w.vel[w.type == 0])
+    return s, err
+
+
+CASES = {
+    "channel_c1": lambda: inputs.channel(10.0, 10.0, 10.0, seed=0),
+    "channel_ragged": lambda: inputs.channel(7.0, 5.0, 5.0, seed=3),
+    "bulk_3cube": lambda: inputs.bulk(3.0, seed=1),
+    "bulk_no_walls": lambda: inputs.bulk((4.0, 5.0, 6.0), seed=2),
+    "channel_tiles": lambda: inputs.channel(24.0, 16.0, 12.0, seed=4),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_initial_force_matches_oracle(name):
+    w = CASES[name]()
+    p = params_for(w, g=(0.02, 0.0, 0.0), seed=123)
+    s, err = _initial_force_parity(w, p)
+    assert err < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_steps_match_oracle_from_identical_state(name):
+    w = CASES[name]()
+    p = params_for(w, g=(0.02, 0.0, 0.0), seed=7)
+    s = make_system(w, p)
+    field = _field(w)
+    seen_reflections = 0
+    for block in range(4):
+        r = compare_one_step(s, w, p, field, label=f"{name} step {block}")
+        seen_reflections += r["reflections"]
+        s.step(4)  # let the GPU run on, then compare again from its own state
+    if "channel" in name:
+        assert seen_reflections > 0 or w.n < 2000
+    s.close()
+
+
+def test_reflect_variant_literal_eq17():
+    w = inputs.channel(6.0, 5.0, 4.0, seed=8)
+    p = params_for(w, g=(0.05, 0.0, 0.0), seed=3, reflect_variant=1)
+    s = make_system(w, p)
+    for _ in range(3):
+        compare_one_step(s, w, p, _field(w), label="variant 1")
+        s.step(5)
+    s.close()
+
+
+def test_body_force_and_parameters_enter_like_the_oracle():
+    w = inputs.channel(6.0, 6.0, 5.0, seed=9)
+    p = params_for(w, g=(0.3, -0.1, 0.05), seed=11, a_ff=18.75, a_fs=40.0, gamma=2.0,
+                   sigma=1.5, lam=0.5, dt=0.005)
+    s = make_system(w, p)
+    for _ in range(3):
+        compare_one_step(s, w, p, _field(w), label="params")
+        s.step(3)
+    s.close()
+
+
+def test_edge_positions_on_the_box_faces():
+    w = inputs.channel(5.0, 4.0, 4.0, seed=10)
+    pos = w.pos.copy()
+    fluid = np.nonzero(w.type == 0)[0]
+    L = np.asarray(w.box, np.float32)
+    pos[fluid[0], 0] = 0.0
+    pos[fluid[1], 0] = np.nextafter(L[0], np.float32(0))
+    pos[fluid[2], 1] = 0.0
+    pos[fluid[3], 1] = np.nextafter(L[1], np.float32(0))
+    w.pos = pos
+    p = params_for(w, seed=5)
+    s, err = _initial_force_parity(w, p)
+    compare_one_step(s, w, p, _field(w), label="faces")
+    s.close()
+
+
+def test_empty_and_all_solid_systems():
+    w = inputs.channel(4.0, 4.0, 3.0, seed=1)
+    p = params_for(w)
+    s = make_system(w, p, load=False)
+    s.set_particles(np.zeros((0, 4), np.float32), np.zeros((0, 4), np.float32),
+                    np.zeros(0, np.int32), np.zeros(0, np.uint8))
+    s.step(3)
+    st = s.stats()
+    assert st[4] == 0 and st[7] == 3
+    solid = w.type != 0
+    ns = int(solid.sum())
+    s.set_particles(w.pos4()[solid], w.vel4()[solid], np.arange(ns, dtype=np.int32),
+                    np.ones(ns, np.uint8))
+    s.step(2)
+    pos, vel, frc, types = gpu_state(s)
+    np.testing.assert_array_equal(pos, w.pos[solid])
+    assert np.all(vel == 0) and np.all(frc == 0)
+    s.close()
+
+
+def test_deterministic_and_graph_replay_is_bitwise_equal():
+    w = inputs.channel(12.0, 8.0, 6.0, seed=12)
+    p = params_for(w, g=(0.02, 0, 0), seed=1)
+    a = make_system(w, p, use_graph=1, graph_steps=10)
+    b = make_system(w, p, use_graph=0)
+    c = make_system(w, p, use_graph=1, graph_steps=4)
+    for s in (a, b, c):
+        s.step(37)
+    ra, rb, rc = (gpu_state(s) for s in (a, b, c))
+    for x, y, z in zip(ra, rb, rc):
+        np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(x, z)
+    for s in (a, b, c):
+        s.close()
+
+
+def test_momentum_conserved_in_periodic_fluid():
+    w = inputs.bulk(8.0, seed=4)
+    p = params_for(w, seed=2)
+    s = make_system(w, p)
+    pos, vel, frc, types = gpu_state(s)
+    fsum = np.abs(frc.astype(np.float64).sum(0))
+    assert fsum.max() <= len(pos) * np.finfo(np.float32).eps * np.abs(frc).max()
+    p0 = s.stats()[:3].copy()
+    s.step(50)
+    p1 = s.stats()[:3]
+    # each step adds at most N * eps32 * max|dt F| of round-off momentum
+    assert np.abs(p1 - p0).max() < 50 * len(pos) * 1e-6
+
+
+def test_profile_sums_match_oracle():
+    w = inputs.channel(8.0, 6.0, 6.0, seed=13)
+    p = params_for(w, g=(0.05, 0, 0), seed=3)
+    s = make_system(w, p)
+    s.step(10)
+    pos, vel, frc, types = gpu_state(s)
+    nb, lo, hi = 24, 0.0, 6.0
+    gpu = s.profile(2, nb, lo, hi, mode=1)
+    ref = oracle.profile(pos, vel.astype(np.float64), types, 2, nb, lo, hi)
+    np.testing.assert_array_equal(gpu[:, 0], ref[:, 0])  # counts: exact
+    np.testing.assert_allclose(gpu[:, 1:], ref[:, 1:], rtol=1e-12, atol=1e-9)
+    # accumulation: a second sample of the same state doubles every sum
+    gpu2 = s.profile(2, nb, lo, hi, mode=0)
+    np.testing.assert_allclose(gpu2, 2 * gpu, rtol=1e-12, atol=1e-9)
+    # automatic sampling inside dpd_step
+    s.profile(2, nb, lo, hi, mode=3)
+    s.set_option("sample_every", 2)
+    s.step(6)
+    acc = s.profile(2, nb, lo, hi, mode=2)
+    assert acc[:, 0].sum() == 3 * (types == 0).sum()
+    s.close()
+
+
+def test_error_codes_are_returned_not_faults():
+    w = inputs.channel(5.0, 5.0, 4.0, seed=14)
+    p = params_for(w)
+    s = make_system(w, p, load=False)
+    with pytest.raises(dpd.DPDError) as e:
+        s.step(1)
+    assert e.value.code == dpd.DPD_ESTATE
+    bad_ids = w.id.copy()
+    bad_ids[1] = bad_ids[0]
+    with pytest.raises(dpd.DPDError) as e:
+        s.set_particles(w.pos4(), w.vel4(), bad_ids, w.type)
+    assert e.value.code == dpd.DPD_EINVAL
+    pos = w.pos4()
+    fl = np.nonzero(w.type == 0)[0][0]
+    pos[fl, 2] = w.gap + 1.0  # a fluid particle in the middle of the solid
+    with pytest.raises(dpd.DPDError) as e:
+        s.set_particles(pos, w.vel4(), w.id, w.type)
+    assert e.value.code == dpd.DPD_ELOST
+    s.set_particles(w.pos4(), w.vel4(), w.id, w.type)
+    s.set_option("band_margin", 0.001)  # drifts of ~0.01 exceed it
+    with pytest.raises(dpd.DPDError) as e:
+        s.step(2)
+    assert e.value.code == dpd.DPD_EBAND
+    with pytest.raises(dpd.DPDError) as e:
+        s.set_option("no_such_option", 1.0)
+    assert e.value.code == dpd.DPD_EINVAL
+    s.close()
+
+
+def test_no_fluid_particle_enters_the_solid_over_a_run():
+    w = inputs.channel(10.0, 10.0, 10.0, seed=15)
+    p = params_for(w, g=(0.02, 0, 0), seed=4)
+    s = make_system(w, p)
+    field = _field(w)
+    for _ in range(10):
+        s.step(50)
+        pos, vel, frc, types = gpu_state(s)
+        assert oracle.phi_many(field, pos[types == 0]).min() >= 0.0
+    assert s.stats()[5] > 0
+    s.close()
+
+
+def test_full_size_channel_one_million():
+    """The benchmark's workload (channel 80 x 64 x 64 gap, ~983k fluid particles)
+    in the benchmark's launch configuration (graph replay): after 20 graph steps
+    one more step is compared particle by particle with the oracle."""
+    w = inputs.channel(80.0, 64.0, 64.0, seed=0)
+    p = params_for(w, g=(0.01, 0.0, 0.0), seed=0)
+    s, err = _initial_force_parity(w, p)
+    s.set_option("use_graph", 1)
+    s.set_option("graph_steps", 20)
+    s.step(20)
+    r = compare_one_step(s, w, p, _field(w), label="1M")
+    assert r["reflections"] > 0
+    s.close()
