@@ -36,17 +36,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic work of the pair-force kernel (derivation in the design notes).
-# Per candidate (a particle of the 27 surrounding cells): 3 subtractions, 3 x
-# (multiply, round, fused multiply-add) of the minimum image, 3 for r^2, 1 compare.
-OPS_PER_CANDIDATE = 16
-# Per pair inside r_c: Philox4x32-10 (10 rounds x (2 mul-hi + 2 mul-lo + 4 xor +
-# 2 key adds) = 100), uniform + Box-Muller (2 shifts, 2 converts, 2 fma, log,
-# sqrt, cospi, 3 mul = 14), pair force (min image 9, r^2 3, rsqrt + 2, weights 2,
-# direction 3, relative velocity 3 + dot 3, magnitude 4, accumulate 3 = 32).
-OPS_PER_PAIR = 146
-# Algorithmic HBM bytes per particle and step of the whole step (design notes).
-BYTES_PER_PARTICLE_STEP = 380
+# Algorithmic work of the pair-force kernel, per fluid particle (the per-unit
+# figures of the design notes): every candidate of the 27 surrounding cells costs
+# ~13 simple ops (separation, minimum image, r^2, compare); every pair inside r_c
+# costs ~115 (Philox4x32-10 ~70 integer ops, Box-Muller ~15, pair force ~30).
+# At rho = 3 with unit cells there are 81 candidates and 4/3 pi rho = 12.57 pairs.
+OPS_PER_CANDIDATE = 13
+OPS_PER_PAIR = 115
+# Algorithmic HBM bytes per particle and step of the whole step: integrate 88,
+# scan 5, scatter 12, per-cell order 13, gather 132, force 96 (design notes).
+BYTES_PER_PARTICLE_STEP = 346
 SM_COUNT_GB300 = 152
 LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
