@@ -134,6 +134,37 @@ int dpd_get_state(dpd_t* h, float* pos4, float* vel4, float* force4, int* id, ui
 int dpd_velocity_profile(dpd_t* h, int axis, int nbins, double lo, double hi, double* out,
                          int mode);
 
+/* Largest nbins accepted by dpd_velocity_profile_noalloc. */
+#define DPD_NOALLOC_MAX_BINS 4096
+
+/* Velocity-profile sums of caller-owned particle arrays, with no memory
+ * allocation of any kind (no cudaMalloc, cudaFree or allocating library call).
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- a framework that owns all device memory through its
+ * own pool, a process under a hard memory cap, or a latency-bound loop where an
+ * allocation would synchronise the device -- and so cannot create a handle.
+ *
+ * pos4, vel4  device arrays of n x 4 floats (x, y, z, unused), any order.
+ * type        device array of n bytes, 0 = fluid (counted), else skipped.
+ * axis, nbins, lo, hi, and the five sums per bin {count, sum vx, sum vy,
+ *             sum vz, sum |v|^2}: as dpd_velocity_profile, for this one sample
+ *             (nothing accumulates across calls); 1 <= nbins <=
+ *             DPD_NOALLOC_MAX_BINS, larger values return DPD_EINVAL.
+ * out         nbins x 5 doubles; host memory (where = DPD_HOST, the call then
+ *             waits for the result) or device memory (DPD_DEVICE, the copy is
+ *             queued on `stream` and the call returns at once).
+ * stream      cudaStream_t to run on (NULL: the default stream).
+ * The FP64 accumulators live in one fixed device array of DPD_NOALLOC_MAX_BINS x
+ * 5 doubles (160 KiB) that every GPU loading the library keeps until the
+ * process exits.  Every call shares it: each call clears what it uses first,
+ * and calls whose work overlaps on the GPU (e.g. on two streams) race and give
+ * wrong sums.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make that first call before any
+ * stream capture begins.  Errors: dpd_last_error(NULL) holds the message. */
+int dpd_velocity_profile_noalloc(const float* pos4, const float* vel4, const uint8_t* type, int n,
+                                 int axis, int nbins, double lo, double hi, double* out, int where,
+                                 void* stream);
+
 /* Whole-system diagnostics, FP64: out[0..2] total fluid momentum, out[3] sum
  * |v|^2 over fluid, out[4] fluid count, out[5] reflections so far, out[6]
  * fallbacks so far (reflected point still at phi < 0, particle kept at r(t)),

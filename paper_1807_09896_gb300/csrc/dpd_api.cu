@@ -71,6 +71,11 @@ static const int kKernelsPerStep = 9;
 
 static std::string g_create_error;
 
+namespace dpd {
+// Message returned by dpd_last_error(NULL), for entry points without a handle.
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace dpd
+
 static int fail(dpd_t* h, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -24,5 +24,6 @@ void launch_load(const StepParams& P, const float4* in_pos, const float4* in_vel
 void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, float4* out_frc,
                    int* out_id, uint8_t* out_type, cudaStream_t s);
 void launch_bump_step(DevCounters* ctr, cudaStream_t s);
+void set_global_error(const char* msg);
 
 }  // namespace dpd

@@ -37,6 +37,7 @@ _SIGS = {
     "dpd_time_phases": (_i, [_vp, _i, _vp]),
     "dpd_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "dpd_velocity_profile": (_i, [_vp, _i, _i, _d, _d, _vp, _i]),
+    "dpd_velocity_profile_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _vp, _i, _vp]),
     "dpd_get_stats": (_i, [_vp, _vp]),
     "dpd_set_option": (_i, [_vp, ctypes.c_char_p, _d]),
     "dpd_get_option": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_d)]),
@@ -169,6 +170,25 @@ def dpd_velocity_profile(h, axis: int, nbins: int, lo: float, hi: float, mode: i
     if out is None and mode != 3:
         out = np.zeros((nbins, 5), np.float64)
     _check(h, load_library().dpd_velocity_profile(h, axis, nbins, lo, hi, _ptr(out), mode))
+    return out
+
+
+NOALLOC_MAX_BINS = 4096
+
+
+def dpd_velocity_profile_noalloc(pos4, vel4, types, n, axis, nbins, lo, hi, out, where=DPD_HOST,
+                                 stream=None):
+    """Allocation-free profile sums of caller-owned device arrays (torch CUDA tensors
+    or raw device pointers) into `out` (numpy array for DPD_HOST, CUDA tensor for
+    DPD_DEVICE).  See include/dpd.h."""
+    s = getattr(stream, "cuda_stream", stream)
+    rc = load_library().dpd_velocity_profile_noalloc(
+        _ptr(pos4) if hasattr(pos4, "data_ptr") else pos4,
+        _ptr(vel4) if hasattr(vel4, "data_ptr") else vel4,
+        _ptr(types) if hasattr(types, "data_ptr") else types, int(n), int(axis), int(nbins),
+        float(lo), float(hi), _ptr(out), int(where), ctypes.c_void_p(s) if s else None)
+    if rc != DPD_OK:
+        raise DPDError(rc, dpd_last_error(None))
     return out
 
 
