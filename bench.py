@@ -264,6 +264,9 @@ def run_ours(args):
             dist.barrier()
 
     s.step(args.warmup)
+    # pick the pair-force launch shape on this device (all shapes are bit-identical)
+    chosen, _ = dpd.dpd_autotune(s.h, 5)
+    s.step(2)
     torch.cuda.synchronize(dev)
     launches0 = s.get_option("kernel_launches")
     uuid = None
@@ -355,6 +358,7 @@ def run_ours(args):
                 "l2": "inputs larger than L2: particle state 2 x %.0f MB + phase field %.0f MB" % (
                     w.n * 64 / 1e6, w.phi.nbytes / 1e6),
                 "graph_steps": 20, "parallelism": f"replicas x{world}",
+                "force_launch_shape": chosen,
             },
             "roofline": {
                 "kernel": "k_force (pair force + closing half-kick)", "bound": "alu",

@@ -117,6 +117,16 @@ enum {
  * milliseconds.  Same results and error codes as dpd_step. */
 int dpd_time_phases(dpd_t* h, int nsteps, double* ms);
 
+/* Pick the fastest launch shape of the pair-force kernel for this system on this
+ * device.  Every shape (threads per block, pair-list slots per thread, resident
+ * blocks, loop unroll) computes bit-identical forces, so the choice affects speed
+ * only.  Each shape is timed over nsteps event-timed steps (after one warm-up
+ * step); the system advances by (nsteps + 1) x (number of shapes) steps.
+ * ms_per_variant (may be NULL) receives the mean force time of each shape (size:
+ * option "force_variants"); chosen (may be NULL) the index now in use (option
+ * "force_variant"). */
+int dpd_autotune(dpd_t* h, int nsteps, double* ms_per_variant, int* chosen);
+
 /* Copy the state in id order: pos4 / vel4 / force4 (n x 4 floats; the force is
  * the pair force f without the body force; solid particles have f = 0), id
  * (n ints, equal to 0..n-1) and type (n bytes).  Any output pointer may be
@@ -176,8 +186,9 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "sample_every",
  * "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
- * default 20).  Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
- * enqueued by stepping calls so far), "kernels_per_step". */
+ * default 20), "force_variant" (launch shape of the pair-force kernel, see
+ * dpd_autotune).  Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
+ * enqueued by stepping calls so far), "kernels_per_step", "force_variants". */
 int dpd_set_option(dpd_t* h, const char* key, double value);
 int dpd_get_option(dpd_t* h, const char* key, double* value);
 

@@ -33,6 +33,7 @@ struct dpd_system {
   int sample_every = 0;
   int use_graph = 1;
   int graph_steps = 20;
+  int force_variant = 0;
   int nc[3] = {0, 0, 0};
   int ncells = 0;
   // phase field
@@ -203,7 +204,7 @@ static void enqueue_step(dpd_t* h, const StepParams& P, int cur) {
   dpd::launch_integrate(P, A, h->cl, h->n, h->d_ctr, h->stream);
   dpd::launch_scan(h->cl, h->ncells, h->n, h->stream);
   dpd::launch_sort(h->cl, A, B, h->n, h->ncells, h->d_ctr, h->stream);
-  dpd::launch_force(P, B, h->cl.start, h->n, h->d_ctr, 1, h->stream);
+  dpd::launch_force(P, B, h->cl.start, h->n, h->d_ctr, 1, h->force_variant, h->stream);
 }
 
 static int status_to_code(dpd_t* h, uint32_t st) {
@@ -359,7 +360,7 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
   dpd::launch_key(P, A, h->cl, n, h->stream);
   dpd::launch_scan(h->cl, h->ncells, n, h->stream);
   dpd::launch_sort(h->cl, A, h->arr[1], n, h->ncells, h->d_ctr, h->stream);
-  dpd::launch_force(P, h->arr[1], h->cl.start, n, h->d_ctr, 0, h->stream);
+  dpd::launch_force(P, h->arr[1], h->cl.start, n, h->d_ctr, 0, h->force_variant, h->stream);
   h->cur = 1;
   cudaError_t le = cudaGetLastError();
   cudaError_t se = cudaStreamSynchronize(h->stream);
@@ -461,7 +462,7 @@ int dpd_time_phases(dpd_t* h, int nsteps, double* ms) {
     cudaEventRecord(ev[2], h->stream);
     dpd::launch_sort(h->cl, A, B, h->n, h->ncells, h->d_ctr, h->stream);
     cudaEventRecord(ev[3], h->stream);
-    dpd::launch_force(P, B, h->cl.start, h->n, h->d_ctr, 1, h->stream);
+    dpd::launch_force(P, B, h->cl.start, h->n, h->d_ctr, 1, h->force_variant, h->stream);
     cudaEventRecord(ev[4], h->stream);
     h->launches += kKernelsPerStep;
     h->cur ^= 1;
@@ -483,6 +484,31 @@ int dpd_time_phases(dpd_t* h, int nsteps, double* ms) {
   rc = read_counters(h);
   if (rc) return rc;
   return status_to_code(h, h->h_ctr->status);
+}
+
+int dpd_autotune(dpd_t* h, int nsteps, double* ms_per_variant, int* chosen) {
+  if (!h) return DPD_EINVAL;
+  if (nsteps <= 0) return fail(h, DPD_EINVAL, "nsteps must be > 0");
+  if (!h->loaded) return fail(h, DPD_ESTATE, "no valid particle state (call dpd_set_particles)");
+  const int nv = dpd::force_variants();
+  int best = h->force_variant;
+  double best_ms = 1e300;
+  for (int v = 0; v < nv; ++v) {
+    h->force_variant = v;
+    double ms[DPD_NPHASES];
+    int rc = dpd_time_phases(h, 1, ms);  // warm-up of this shape
+    if (rc == DPD_OK) rc = dpd_time_phases(h, nsteps, ms);
+    if (rc != DPD_OK) return rc;
+    if (ms_per_variant) ms_per_variant[v] = ms[DPD_PHASE_FORCE];
+    if (ms[DPD_PHASE_FORCE] < best_ms) {
+      best_ms = ms[DPD_PHASE_FORCE];
+      best = v;
+    }
+  }
+  h->force_variant = best;
+  free_graphs(h);
+  if (chosen) *chosen = best;
+  return DPD_OK;
 }
 
 int dpd_get_state(dpd_t* h, float* pos4, float* vel4, float* force4, int* id, uint8_t* type,
@@ -603,6 +629,10 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     h->host_step = s;
   } else if (k == "use_graph") {
     h->use_graph = v != 0.0;
+  } else if (k == "force_variant") {
+    if (v < 0 || v >= dpd::force_variants() || v != std::floor(v))
+      return fail(h, DPD_EINVAL, "force_variant must be an integer in [0, %d)", dpd::force_variants());
+    h->force_variant = (int)v;
   } else if (k == "graph_steps") {
     if (v < 2 || v > 1000 || v != std::floor(v) || ((int)v & 1))
       return fail(h, DPD_EINVAL, "graph_steps must be an even number in [2, 1000]");
@@ -628,6 +658,8 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "graph_steps") *v = h->graph_steps;
   else if (k == "ncells") *v = h->ncells;
   else if (k == "kernel_launches") *v = (double)h->launches;
+  else if (k == "force_variant") *v = h->force_variant;
+  else if (k == "force_variants") *v = dpd::force_variants();
   else if (k == "kernels_per_step") *v = kKernelsPerStep;
   else return fail(h, DPD_EINVAL, "unknown option '%s'", key);
   return DPD_OK;

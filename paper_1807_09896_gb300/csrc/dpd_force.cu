@@ -21,10 +21,12 @@
 
 namespace dpd {
 
-constexpr int kForceThreads = 128;
-constexpr int kListCap = 24;
-
-__global__ void __launch_bounds__(kForceThreads)
+// Launch shapes (threads per block, pair-list slots per thread, minimum resident
+// blocks per SM, unroll of the pair loop).  Every shape sums the same pairs in
+// the same order, so all of them give bit-identical forces; dpd_autotune picks
+// the fastest on the device at hand.
+template <int kForceThreads, int kListCap, int kMinBlocks, int kUnroll>
+__global__ void __launch_bounds__(kForceThreads, kMinBlocks)
 k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCounters* ctr,
         int kick) {
   __shared__ int list[kListCap][kForceThreads];
@@ -41,14 +43,67 @@ k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCo
   float fx = 0.f, fy = 0.f, fz = 0.f;
   int cnt = 0;
 
-  auto flush = [&]() {
-    for (int k = 0; k < cnt; ++k) {
-      const int j = list[k][threadIdx.x];
+  // Neighbour cells are visited as segments: for a particle away from the x seam
+  // one segment per (dy, dz) row covers the three x-neighbour cells, which are
+  // contiguous in cell order; on the seam every cell is its own segment.  Within
+  // a segment the periodic image is fixed: d = t - (x_j - c), with t the target
+  // coordinate shifted by -L when the cells lie across the upper seam and c = L
+  // when they lie across the lower seam.  Both shifts are exact (the shifted
+  // coordinate lies in [L/2, L)), and for every pair inside r_c the result equals
+  // the minimum-image separation bit for bit.
+  const int cx = cell_coord(pi.x, P.inv_edge[0], P.nc[0]);
+  const int cy = cell_coord(pi.y, P.inv_edge[1], P.nc[1]);
+  const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
+  const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
+  const bool inner = cx > 0 && cx < ncx - 1;
+  const int nseg = inner ? 9 : 27;
+  int seg = 0;
+  uint32_t j = 0, e = 0;
+  float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
+  for (;;) {
+    // fill the list with candidates inside r_c until it is full or the cells run out
+    while (cnt < kListCap) {
+      if (j == e) {
+        if (seg == nseg) break;
+        const int part = inner ? 1 : seg % 3;
+        const int rowi = inner ? seg : seg / 3;
+        const int dy = rowi % 3 - 1, dz = rowi / 3 - 1;
+        int z = cz + dz, y = cy + dy;
+        tz = pi.z; sz = 0.f; ty = pi.y; sy = 0.f;
+        if (z < 0) { z += ncz; sz = P.L[2]; } else if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
+        if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
+        const int row = (z * ncy + y) * ncx;
+        if (inner) {
+          j = __ldg(&start[row + cx - 1]);
+          e = __ldg(&start[row + cx + 2]);
+          tx = pi.x; sx = 0.f;
+        } else {
+          int x = cx + part - 1;
+          tx = pi.x; sx = 0.f;
+          if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
+          j = __ldg(&start[row + x]);
+          e = __ldg(&start[row + x + 1]);
+        }
+        ++seg;
+        continue;
+      }
       const float4 pj = __ldg(&pos[j]);
+      const float dx = tx - (pj.x - sx);
+      const float dy = ty - (pj.y - sy);
+      const float dz = tz - (pj.z - sz);
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (r2 < 1.0f && r2 > 0.0f) list[cnt++][threadIdx.x] = (int)j;
+      ++j;
+    }
+    // evaluate the listed pairs
+#pragma unroll kUnroll
+    for (int k = 0; k < cnt; ++k) {
+      const int jj = list[k][threadIdx.x];
+      const float4 pj = __ldg(&pos[jj]);
       const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
       const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
       const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const float inv_r = rsqrtf(r2);
       const float r = r2 * inv_r;
       const float w = 1.0f - r;
@@ -58,7 +113,7 @@ k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCo
         vjx = P.vw[0]; vjy = P.vw[1]; vjz = P.vw[2];
         a = P.a_fs;
       } else {
-        const float4 vtj = __ldg(&vt[j]);
+        const float4 vtj = __ldg(&vt[jj]);
         vjx = vtj.x; vjy = vtj.y; vjz = vtj.z;
         a = P.a_ff;
       }
@@ -69,46 +124,9 @@ k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCo
       fy = fmaf(mag, ey, fy);
       fz = fmaf(mag, ez, fz);
     }
+    if (cnt < kListCap) break;  // the cells ran out before the list filled
     cnt = 0;
-  };
-
-  auto scan = [&](uint32_t b, uint32_t e) {
-    for (uint32_t j = b; j < e; ++j) {
-      const float4 pj = __ldg(&pos[j]);
-      const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
-      const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
-      const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < 1.0f && r2 > 0.0f) {
-        list[cnt][threadIdx.x] = (int)j;
-        if (++cnt == kListCap) flush();
-      }
-    }
-  };
-
-  const int cx = cell_coord(pi.x, P.inv_edge[0], P.nc[0]);
-  const int cy = cell_coord(pi.y, P.inv_edge[1], P.nc[1]);
-  const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
-  const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
-  for (int dz = -1; dz <= 1; ++dz) {
-    int z = cz + dz;
-    z = z < 0 ? z + ncz : (z >= ncz ? z - ncz : z);
-    for (int dy = -1; dy <= 1; ++dy) {
-      int y = cy + dy;
-      y = y < 0 ? y + ncy : (y >= ncy ? y - ncy : y);
-      const int row = (z * ncy + y) * ncx;
-      if (cx > 0 && cx < ncx - 1) {
-        scan(__ldg(&start[row + cx - 1]), __ldg(&start[row + cx + 2]));
-      } else {
-        for (int dx = -1; dx <= 1; ++dx) {
-          int x = cx + dx;
-          x = x < 0 ? x + ncx : (x >= ncx ? x - ncx : x);
-          scan(__ldg(&start[row + x]), __ldg(&start[row + x + 1]));
-        }
-      }
-    }
   }
-  flush();
 
   const float4 f_old = A.frc[i];
   A.frc[i] = make_float4(fx, fy, fz, 0.0f);
@@ -124,11 +142,32 @@ k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCo
     atomicOr(&ctr->status, ST_NAN);
 }
 
+struct ForceVariant {
+  void (*kernel)(StepParams, Arrays, const uint32_t*, int, DevCounters*, int);
+  int threads;
+};
+
+static const ForceVariant kForceVariants[] = {
+    {k_force<128, 24, 1, 1>, 128}, {k_force<128, 16, 1, 1>, 128}, {k_force<256, 16, 1, 1>, 256},
+    {k_force<64, 24, 1, 1>, 64},   {k_force<128, 16, 12, 1>, 128}, {k_force<256, 12, 6, 1>, 256},
+    {k_force<128, 32, 1, 1>, 128}, {k_force<128, 24, 1, 2>, 128}, {k_force<128, 16, 12, 2>, 128},
+};
+
+int force_variants() { return (int)(sizeof(kForceVariants) / sizeof(kForceVariants[0])); }
+
+const char* force_variant_name(int v) {
+  static const char* names[] = {"128x24", "128x16", "256x16", "64x24", "128x16/min12",
+                                "256x12/min6", "128x32", "128x24/unroll2", "128x16/min12/unroll2"};
+  return (v >= 0 && v < force_variants()) ? names[v] : "?";
+}
+
 void launch_force(const StepParams& P, const Arrays& A, const uint32_t* start, int n,
-                  DevCounters* ctr, int kick, cudaStream_t s) {
+                  DevCounters* ctr, int kick, int variant, cudaStream_t s) {
   if (n <= 0) return;
-  const int nb = (n + kForceThreads - 1) / kForceThreads;
-  k_force<<<nb, kForceThreads, 0, s>>>(P, A, start, n, ctr, kick);
+  if (variant < 0 || variant >= force_variants()) variant = 0;
+  const ForceVariant& fv = kForceVariants[variant];
+  const int nb = (n + fv.threads - 1) / fv.threads;
+  fv.kernel<<<nb, fv.threads, 0, s>>>(P, A, start, n, ctr, kick);
 }
 
 }  // namespace dpd

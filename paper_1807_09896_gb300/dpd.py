@@ -35,6 +35,7 @@ _SIGS = {
     "dpd_set_particles": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i]),
     "dpd_step": (_i, [_vp, _i]),
     "dpd_time_phases": (_i, [_vp, _i, _vp]),
+    "dpd_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
     "dpd_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "dpd_velocity_profile": (_i, [_vp, _i, _i, _d, _d, _vp, _i]),
     "dpd_velocity_profile_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _vp, _i, _vp]),
@@ -141,6 +142,16 @@ def dpd_time_phases(h, nsteps: int) -> dict:
     ms = np.zeros(len(PHASES), np.float64)
     _check(h, load_library().dpd_time_phases(h, int(nsteps), _ptr(ms)))
     return dict(zip(PHASES, ms.tolist()))
+
+
+def dpd_autotune(h, nsteps: int = 5):
+    """Time every launch shape of the force kernel; keep the fastest.  Returns
+    (chosen index, list of mean force ms per shape)."""
+    nv = int(dpd_get_option(h, "force_variants"))
+    ms = np.zeros(nv, np.float64)
+    chosen = ctypes.c_int()
+    _check(h, load_library().dpd_autotune(h, int(nsteps), _ptr(ms), ctypes.byref(chosen)))
+    return chosen.value, ms.tolist()
 
 
 def dpd_num_particles(h):

@@ -245,3 +245,35 @@ def test_full_size_channel_one_million():
     r = compare_one_step(s, w, p, _field(w), label="1M")
     assert r["reflections"] > 0
     s.close()
+
+
+def test_every_force_launch_shape_gives_bitwise_identical_steps():
+    w = inputs.channel(9.0, 7.0, 6.0, seed=16)
+    p = params_for(w, g=(0.02, 0, 0), seed=6)
+    ref = None
+    nv = int(make_system(w, p, load=False).get_option("force_variants"))
+    for v in range(nv):
+        s = make_system(w, p, load=False, force_variant=v)
+        s.set_particles(w.pos4(), w.vel4(), w.id, w.type)
+        s.step(7)
+        st = gpu_state(s)
+        if ref is None:
+            ref = st
+        else:
+            for x, y in zip(ref, st):
+                np.testing.assert_array_equal(x, y)
+        s.close()
+
+
+def test_autotune_keeps_results_and_picks_a_shape():
+    w = inputs.channel(10.0, 8.0, 6.0, seed=17)
+    p = params_for(w, seed=8)
+    a = make_system(w, p)
+    b = make_system(w, p)
+    chosen, ms = dpd.dpd_autotune(a.h, 2)
+    assert 0 <= chosen < len(ms) and all(m > 0 for m in ms)
+    assert a.get_option("force_variant") == chosen
+    steps_done = int(a.get_option("step"))
+    b.step(steps_done)
+    for x, y in zip(gpu_state(a), gpu_state(b)):
+        np.testing.assert_array_equal(x, y)
