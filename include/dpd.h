@@ -195,6 +195,41 @@ int dpd_get_option(dpd_t* h, const char* key, double* value);
 /* Particle counts currently loaded. */
 int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
 
+/* ---- Batches: many independent systems advanced together ------------------
+ * The paper has no counterpart (it runs one system at a time); this is the
+ * ensemble form of the same step.  A batch copies the current state of nsys
+ * loaded systems into one set of concatenated device arrays; every phase of a
+ * step is then one launch over all systems, replayed from a CUDA graph.  Each
+ * system keeps its own box, phase field, parameters, seed, system index and step
+ * counter: a system advanced in a batch follows bit for bit the trajectory it
+ * follows alone.  The member handles are not advanced (their state stays as it
+ * was at dpd_batch_create); the batch reads their phase fields and band masks,
+ * so they must outlive the batch and keep their phase field.  Error messages of
+ * dpd_batch_create: dpd_batch_last_error(NULL). */
+typedef struct dpd_batch dpd_batch_t;
+
+int dpd_batch_create(dpd_batch_t** hb, int nsys, dpd_t* const* systems);
+/* Advance every system by nsteps steps (graph replay; options "use_graph",
+ * "graph_steps" as for a single system).  Errors as dpd_step. */
+int dpd_batch_step(dpd_batch_t* hb, int nsteps);
+/* As dpd_time_phases / dpd_autotune, over the whole batch. */
+int dpd_batch_time_phases(dpd_batch_t* hb, int nsteps, double* ms);
+int dpd_batch_autotune(dpd_batch_t* hb, int nsteps, double* ms_per_variant, int* chosen);
+/* State of system k (0-based, in the order given to dpd_batch_create), in its
+ * own id order; arguments as dpd_get_state. */
+int dpd_batch_get_state(dpd_batch_t* hb, int k, float* pos4, float* vel4, float* force4, int* id,
+                        uint8_t* type, int where);
+/* Diagnostics of system k, as dpd_get_stats. */
+int dpd_batch_get_stats(dpd_batch_t* hb, int k, double out[8]);
+/* Options "use_graph", "graph_steps", "force_variant"; read-only "force_variants",
+ * "kernel_launches", "kernels_per_step", "nsys", "n" (all particles), "ncells". */
+int dpd_batch_set_option(dpd_batch_t* hb, const char* key, double value);
+int dpd_batch_get_option(dpd_batch_t* hb, const char* key, double* value);
+int dpd_batch_num_particles(dpd_batch_t* hb, int k, int* n, int* n_fluid);
+int dpd_batch_set_stream(dpd_batch_t* hb, void* stream);
+int dpd_batch_destroy(dpd_batch_t* hb);
+const char* dpd_batch_last_error(const dpd_batch_t* hb);
+
 /* Run the handle's work on `stream` (a cudaStream_t; NULL selects the handle's
  * own stream). */
 int dpd_set_stream(dpd_t* h, void* stream);

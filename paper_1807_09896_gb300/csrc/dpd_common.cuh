@@ -50,6 +50,28 @@ struct StepParams {
   const uint8_t* band;  // per cell: 1 if a particle starting there may reach phi < 0
 };
 
+// One system of a batch: its parameters and where its cells and particles sit
+// in the concatenated arrays (a single system is a batch of one).  Systems
+// occupy contiguous, increasing ranges of cells, hence of particles in cell
+// order, and keep their particle counts, so the ranges never move.
+struct SysDesc {
+  StepParams P;
+  uint32_t cell_off;
+  uint32_t part_off;
+  uint32_t n;
+  uint32_t pad;
+};
+
+// System of particle i: the last system whose particle range starts at or below i.
+__device__ __forceinline__ int sys_of(const SysDesc* __restrict__ S, int nsys, uint32_t i) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S[mid].part_off <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 struct Arrays {
   float4* pos;
   float4* vt;

@@ -1,0 +1,288 @@
+// dpd_engine.cu -- launch sequence of one DPD time step over one or more
+// independent systems (Xu & Meakin, arXiv:1807.09896, Sec. II): counter bump,
+// drift + reflection + cell key, scan, counting sort, pair force + closing kick.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/dpd.h"
+#include "dpd_engine.h"
+#include "dpd_launch.h"
+
+namespace dpd {
+
+int engine_fail(Engine& E, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (E.err) *E.err = buf;
+  return code;
+}
+
+#define ECU(E, call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return engine_fail((E), DPD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+template <typename T>
+static cudaError_t dev_alloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+void engine_free_graphs(Engine& E) {
+  for (auto& g : E.graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+static void free_particle_buffers(Engine& E) {
+  for (auto& A : E.arr) {
+    cudaFree(A.pos);
+    cudaFree(A.vt);
+    cudaFree(A.vel);
+    cudaFree(A.frc);
+    A = Arrays{};
+  }
+  cudaFree(E.cl.key);
+  cudaFree(E.cl.rank);
+  cudaFree(E.cl.perm);
+  E.cl.key = E.cl.rank = E.cl.perm = nullptr;
+  E.cap = 0;
+}
+
+static void free_cell_buffers(Engine& E) {
+  cudaFree(E.cl.count);
+  cudaFree(E.cl.start);
+  cudaFree(E.cl.blocksum);
+  E.cl.count = E.cl.start = E.cl.blocksum = nullptr;
+  E.cell_cap = 0;
+}
+
+void engine_free(Engine& E) {
+  if (E.stream) cudaStreamSynchronize(E.stream);
+  engine_free_graphs(E);
+  free_particle_buffers(E);
+  free_cell_buffers(E);
+  cudaFree(E.d_sys);
+  cudaFree(E.d_ctr);
+  if (E.h_ctr) cudaFreeHost(E.h_ctr);
+  E.d_sys = nullptr;
+  E.d_ctr = nullptr;
+  E.h_ctr = nullptr;
+  E.sys_cap = 0;
+}
+
+int engine_reserve(Engine& E, int nsys, int n, int ncells) {
+  if (nsys > E.sys_cap) {
+    engine_free_graphs(E);
+    cudaFree(E.d_sys);
+    cudaFree(E.d_ctr);
+    if (E.h_ctr) cudaFreeHost(E.h_ctr);
+    E.d_sys = nullptr;
+    E.d_ctr = nullptr;
+    E.h_ctr = nullptr;
+    E.sys_cap = 0;
+    ECU(E, dev_alloc(&E.d_sys, nsys));
+    ECU(E, dev_alloc(&E.d_ctr, nsys));
+    ECU(E, cudaMallocHost((void**)&E.h_ctr, sizeof(DevCounters) * nsys));
+    ECU(E, cudaMemsetAsync(E.d_ctr, 0, sizeof(DevCounters) * nsys, E.stream));
+    memset(E.h_ctr, 0, sizeof(DevCounters) * nsys);
+    E.sys_cap = nsys;
+  }
+  if (ncells > E.cell_cap) {
+    engine_free_graphs(E);
+    free_cell_buffers(E);
+    ECU(E, dev_alloc(&E.cl.count, ncells));
+    ECU(E, dev_alloc(&E.cl.start, (size_t)ncells + 1));
+    ECU(E, dev_alloc(&E.cl.blocksum, scan_blocks(ncells)));
+    E.cell_cap = ncells;
+  }
+  if (n > E.cap) {
+    engine_free_graphs(E);
+    free_particle_buffers(E);
+    for (auto& A : E.arr) {
+      ECU(E, dev_alloc(&A.pos, n));
+      ECU(E, dev_alloc(&A.vt, n));
+      ECU(E, dev_alloc(&A.vel, n));
+      ECU(E, dev_alloc(&A.frc, n));
+    }
+    ECU(E, dev_alloc(&E.cl.key, n));
+    ECU(E, dev_alloc(&E.cl.rank, n));
+    ECU(E, dev_alloc(&E.cl.perm, n));
+    E.cap = n;
+  }
+  E.nsys = nsys;
+  E.n = n;
+  E.ncells = ncells;
+  // counts must start at zero; every scan leaves them at zero
+  ECU(E, cudaMemsetAsync(E.cl.count, 0, sizeof(uint32_t) * (ncells > 0 ? ncells : 1), E.stream));
+  return DPD_OK;
+}
+
+int engine_upload_sys(Engine& E) {
+  ECU(E, cudaMemcpyAsync(E.d_sys, E.h_sys.data(), sizeof(SysDesc) * E.nsys, cudaMemcpyHostToDevice,
+                         E.stream));
+  ECU(E, cudaStreamSynchronize(E.stream));
+  return DPD_OK;
+}
+
+void engine_enqueue_sort(Engine& E) {
+  launch_key(E.d_sys, E.nsys, E.arr[E.cur], E.cl, E.n, E.stream);
+  launch_scan(E.cl, E.ncells, E.n, E.stream);
+  launch_sort(E.cl, E.arr[E.cur], E.arr[E.cur ^ 1], E.n, E.ncells, E.d_ctr, E.stream);
+  E.cur ^= 1;
+}
+
+void engine_enqueue_force(Engine& E, int kick) {
+  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, E.arr[E.cur], E.cl.start, E.n, E.d_ctr, kick,
+               E.force_variant, E.stream);
+}
+
+// One step from arr[c] into arr[c ^ 1] (does not touch E.cur).
+static void enqueue_step_from(Engine& E, int c) {
+  const Arrays& A = E.arr[c];
+  const Arrays& B = E.arr[c ^ 1];
+  launch_bump_step(E.d_ctr, E.nsys, E.stream);
+  launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
+  launch_scan(E.cl, E.ncells, E.n, E.stream);
+  launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
+  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.n, E.d_ctr, 1, E.force_variant,
+               E.stream);
+}
+
+void engine_enqueue_step(Engine& E) {
+  enqueue_step_from(E, E.cur);
+  E.cur ^= 1;
+  E.launches += kKernelsPerStep;
+}
+
+static int build_graph(Engine& E, int c) {
+  cudaGraph_t g = nullptr;
+  ECU(E, cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal));
+  int cc = c;
+  for (int k = 0; k < E.graph_steps; ++k) {
+    enqueue_step_from(E, cc);
+    cc ^= 1;
+  }
+  cudaError_t e = cudaStreamEndCapture(E.stream, &g);
+  if (e != cudaSuccess)
+    return engine_fail(E, DPD_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&E.graph[c], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    E.graph[c] = nullptr;
+    return engine_fail(E, DPD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  return DPD_OK;
+}
+
+int engine_step(Engine& E, int nsteps) {
+  int left = nsteps;
+  while (left > 0) {
+    if (E.use_graph && left >= E.graph_steps) {
+      if (!E.graph[E.cur]) {
+        const int rc = build_graph(E, E.cur);
+        if (rc) return rc;
+      }
+      ECU(E, cudaGraphLaunch(E.graph[E.cur], E.stream));
+      // graph_steps is even: the state ends in the buffers it started in
+      E.launches += (uint64_t)kKernelsPerStep * E.graph_steps;
+      left -= E.graph_steps;
+      continue;
+    }
+    engine_enqueue_step(E);
+    left -= 1;
+  }
+  ECU(E, cudaGetLastError());
+  return DPD_OK;
+}
+
+int engine_time_phases(Engine& E, int nsteps, double* ms) {
+  cudaEvent_t ev[DPD_NPHASES + 1];
+  for (auto& e : ev) ECU(E, cudaEventCreate(&e));
+  double acc[DPD_NPHASES] = {0};
+  int rc = DPD_OK;
+  for (int k = 0; k < nsteps && rc == DPD_OK; ++k) {
+    const Arrays& A = E.arr[E.cur];
+    const Arrays& B = E.arr[E.cur ^ 1];
+    cudaEventRecord(ev[0], E.stream);
+    launch_bump_step(E.d_ctr, E.nsys, E.stream);
+    launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
+    cudaEventRecord(ev[1], E.stream);
+    launch_scan(E.cl, E.ncells, E.n, E.stream);
+    cudaEventRecord(ev[2], E.stream);
+    launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
+    cudaEventRecord(ev[3], E.stream);
+    launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.n, E.d_ctr, 1, E.force_variant,
+                 E.stream);
+    cudaEventRecord(ev[4], E.stream);
+    E.launches += kKernelsPerStep;
+    E.cur ^= 1;
+    const cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) {
+      rc = engine_fail(E, DPD_ECUDA, "timed step failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (int q = 0; q < DPD_NPHASES; ++q) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+      acc[q] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (int q = 0; q < DPD_NPHASES; ++q) ms[q] = acc[q] / nsteps;
+  return DPD_OK;
+}
+
+int engine_autotune(Engine& E, int nsteps, double* ms_per_variant, int* chosen) {
+  const int nv = force_variants();
+  int best = E.force_variant;
+  double best_ms = 1e300;
+  for (int v = 0; v < nv; ++v) {
+    E.force_variant = v;
+    double ms[DPD_NPHASES];
+    int rc = engine_time_phases(E, 1, ms);  // warm-up of this shape
+    if (rc == DPD_OK) rc = engine_time_phases(E, nsteps, ms);
+    if (rc != DPD_OK) return rc;
+    if (ms_per_variant) ms_per_variant[v] = ms[DPD_PHASE_FORCE];
+    if (ms[DPD_PHASE_FORCE] < best_ms) {
+      best_ms = ms[DPD_PHASE_FORCE];
+      best = v;
+    }
+  }
+  E.force_variant = best;
+  engine_free_graphs(E);
+  if (chosen) *chosen = best;
+  return DPD_OK;
+}
+
+int engine_read_counters(Engine& E, uint32_t* status) {
+  ECU(E, cudaMemcpyAsync(E.h_ctr, E.d_ctr, sizeof(DevCounters) * E.nsys, cudaMemcpyDeviceToHost,
+                         E.stream));
+  ECU(E, cudaStreamSynchronize(E.stream));
+  uint32_t st = 0;
+  for (int k = 0; k < E.nsys; ++k) st |= E.h_ctr[k].status;
+  *status = st;
+  return DPD_OK;
+}
+
+int engine_status_code(Engine& E, uint32_t st) {
+  if (st == 0) return DPD_OK;
+  if (st & ST_NAN) return engine_fail(E, DPD_ENAN, "non-finite position, velocity or force");
+  if (st & ST_LOST) return engine_fail(E, DPD_ELOST, "a fluid particle is at phi < 0");
+  if (st & ST_BADID) return engine_fail(E, DPD_EINVAL, "ids are not a permutation of 0..n-1");
+  if (st & ST_OVERFLOW)
+    return engine_fail(E, DPD_EOVERFLOW, "a cell holds more particles than the sort capacity");
+  if (st & ST_BAND)
+    return engine_fail(E, DPD_EBAND,
+                       "a drift exceeded the band margin; reduce dt or raise band_margin");
+  return engine_fail(E, DPD_ECUDA, "unknown device status %#x", st);
+}
+
+}  // namespace dpd

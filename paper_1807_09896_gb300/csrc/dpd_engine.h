@@ -1,0 +1,61 @@
+// dpd_engine.h -- the device state and launch sequence of DPD time steps for one
+// or more independent systems held in concatenated arrays (internal).
+//
+// A single system (dpd_t) is an engine with one system; a batch (dpd_batch_t)
+// is an engine with many.  Every phase of a step is one launch over all systems.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dpd_common.cuh"
+
+namespace dpd {
+
+// Kernels one time step enqueues: counter bump, drift/reflect/key, three scan
+// passes, scatter, per-cell sort, gather, force.
+constexpr int kKernelsPerStep = 9;
+
+struct Engine {
+  int nsys = 0, n = 0, ncells = 0;
+  int cap = 0, cell_cap = 0, sys_cap = 0;
+  Arrays arr[2] = {};
+  int cur = 0;  // arrays holding the current state
+  CellList cl = {};
+  SysDesc* d_sys = nullptr;
+  std::vector<SysDesc> h_sys;
+  DevCounters* d_ctr = nullptr;  // one per system
+  DevCounters* h_ctr = nullptr;  // pinned mirror
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int use_graph = 1, graph_steps = 20, force_variant = 0;
+  uint64_t launches = 0;
+  std::string* err = nullptr;  // where failure messages go
+};
+
+int engine_fail(Engine& E, int code, const char* fmt, ...);
+// Grow buffers to hold nsys systems, n particles and ncells cells (never shrinks).
+int engine_reserve(Engine& E, int nsys, int n, int ncells);
+// Copy the host system table to the device (waits for the copy).
+int engine_upload_sys(Engine& E);
+void engine_free_graphs(Engine& E);
+void engine_free(Engine& E);
+// Cell build of the state in arr[cur] into arr[cur ^ 1] (set-up, nothing moves).
+void engine_enqueue_sort(Engine& E);
+// Pair force on arr[cur]; kick = 1 adds the closing half-kick.
+void engine_enqueue_force(Engine& E, int kick);
+// One full time step from arr[cur]; flips cur.
+void engine_enqueue_step(Engine& E);
+// nsteps steps, replayed from CUDA graphs where possible.  Does not wait.
+int engine_step(Engine& E, int nsteps);
+// nsteps steps launched one by one with events between phases; mean ms per phase.
+int engine_time_phases(Engine& E, int nsteps, double* ms);
+// Time every force launch shape; keep the fastest.
+int engine_autotune(Engine& E, int nsteps, double* ms_per_variant, int* chosen);
+// Copy the counters to the host (waits); *status = OR of every system's status.
+int engine_read_counters(Engine& E, uint32_t* status);
+// Error code and message for a non-zero status word.
+int engine_status_code(Engine& E, uint32_t status);
+
+}  // namespace dpd

@@ -25,15 +25,10 @@ namespace dpd {
 // blocks per SM, unroll of the pair loop).  Every shape sums the same pairs in
 // the same order, so all of them give bit-identical forces; dpd_autotune picks
 // the fastest on the device at hand.
-template <int kForceThreads, int kListCap, int kMinBlocks, int kUnroll>
-__global__ void __launch_bounds__(kForceThreads, kMinBlocks)
-k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCounters* ctr,
-        int kick) {
-  __shared__ int list[kListCap][kForceThreads];
-  const int i = blockIdx.x * kForceThreads + threadIdx.x;
-  if (i >= n) return;
-  const float4 pi = A.pos[i];
-  if (is_solid(pi.w)) return;
+template <int kForceThreads, int kListCap, int kUnroll>
+__device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* __restrict__ start,
+                                           DevCounters* ctr, const Arrays& A, int i, float4 pi,
+                                           int (*list)[kForceThreads], int kick) {
   const float4 vti = A.vt[i];
   const uint32_t idi = id_of(pi.w);
   const uint32_t step = ctr->step;
@@ -142,15 +137,44 @@ k_force(StepParams P, Arrays A, const uint32_t* __restrict__ start, int n, DevCo
     atomicOr(&ctr->status, ST_NAN);
 }
 
+// A single system takes its parameters by value (they stay in the kernel-parameter
+// bank); a batch reads each particle's system from the table.  Both run the same
+// body, so a system computes the same bits alone and in a batch.
+template <int kForceThreads, int kListCap, int kMinBlocks, int kUnroll, bool kBatch>
+__global__ void __launch_bounds__(kForceThreads, kMinBlocks)
+k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
+        const uint32_t* __restrict__ start_all, int n, DevCounters* ctrs, int kick) {
+  __shared__ int list[kListCap][kForceThreads];
+  const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 pi = A.pos[i];
+  if (is_solid(pi.w)) return;
+  if constexpr (kBatch) {
+    const int sk = sys_of(S, nsys, (uint32_t)i);
+    force_body<kForceThreads, kListCap, kUnroll>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk, A,
+                                                 i, pi, list, kick);
+  } else {
+    force_body<kForceThreads, kListCap, kUnroll>(P0, start_all, ctrs, A, i, pi, list, kick);
+  }
+}
+
+using ForceKernel = void (*)(StepParams, const SysDesc*, int, Arrays, const uint32_t*, int,
+                             DevCounters*, int);
+
 struct ForceVariant {
-  void (*kernel)(StepParams, Arrays, const uint32_t*, int, DevCounters*, int);
+  ForceKernel single, batch;
   int threads;
 };
 
+#define DPD_FORCE_VARIANT(T, C, M, U) \
+  { k_force<T, C, M, U, false>, k_force<T, C, M, U, true>, T }
+
 static const ForceVariant kForceVariants[] = {
-    {k_force<128, 24, 1, 1>, 128}, {k_force<128, 16, 1, 1>, 128}, {k_force<256, 16, 1, 1>, 256},
-    {k_force<64, 24, 1, 1>, 64},   {k_force<128, 16, 12, 1>, 128}, {k_force<256, 12, 6, 1>, 256},
-    {k_force<128, 32, 1, 1>, 128}, {k_force<128, 24, 1, 2>, 128}, {k_force<128, 16, 12, 2>, 128},
+    DPD_FORCE_VARIANT(128, 24, 1, 1), DPD_FORCE_VARIANT(128, 16, 1, 1),
+    DPD_FORCE_VARIANT(256, 16, 1, 1), DPD_FORCE_VARIANT(64, 24, 1, 1),
+    DPD_FORCE_VARIANT(128, 16, 12, 1), DPD_FORCE_VARIANT(256, 12, 6, 1),
+    DPD_FORCE_VARIANT(128, 32, 1, 1), DPD_FORCE_VARIANT(128, 24, 1, 2),
+    DPD_FORCE_VARIANT(128, 16, 12, 2),
 };
 
 int force_variants() { return (int)(sizeof(kForceVariants) / sizeof(kForceVariants[0])); }
@@ -161,13 +185,14 @@ const char* force_variant_name(int v) {
   return (v >= 0 && v < force_variants()) ? names[v] : "?";
 }
 
-void launch_force(const StepParams& P, const Arrays& A, const uint32_t* start, int n,
-                  DevCounters* ctr, int kick, int variant, cudaStream_t s) {
+void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                  const uint32_t* start, int n, DevCounters* ctr, int kick, int variant,
+                  cudaStream_t s) {
   if (n <= 0) return;
   if (variant < 0 || variant >= force_variants()) variant = 0;
   const ForceVariant& fv = kForceVariants[variant];
   const int nb = (n + fv.threads - 1) / fv.threads;
-  fv.kernel<<<nb, fv.threads, 0, s>>>(P, A, start, n, ctr, kick);
+  (nsys == 1 ? fv.single : fv.batch)<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, n, ctr, kick);
 }
 
 }  // namespace dpd

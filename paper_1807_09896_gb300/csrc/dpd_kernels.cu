@@ -40,10 +40,9 @@ __device__ __forceinline__ float wrap_coord(float x, float L) {
   return x;
 }
 
-__global__ void __launch_bounds__(256) k_integrate(StepParams P, Arrays A, CellList C, int n,
-                                                   DevCounters* ctr) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cell_off,
+                                               DevCounters* ctr, const Arrays& A,
+                                               const CellList& C, int i) {
   float4 p = A.pos[i];
   if (!is_solid(p.w)) {
     const float4 v = A.vel[i];
@@ -94,17 +93,34 @@ __global__ void __launch_bounds__(256) k_integrate(StepParams P, Arrays A, CellL
     A.pos[i] = p;
     A.vt[i] = vt;
   }
-  const int c = cell_of(P, p.x, p.y, p.z);
-  C.key[i] = (uint32_t)c;
+  const uint32_t c = cell_off + (uint32_t)cell_of(P, p.x, p.y, p.z);
+  C.key[i] = c;
   C.rank[i] = atomicAdd(&C.count[c], 1u);
 }
 
-// Cell key only (set-up: particles loaded, nothing moves).
-__global__ void k_key(StepParams P, Arrays A, CellList C, int n) {
+// A single system takes its parameters by value (kernel-parameter bank); a batch
+// reads each particle's system from the table.  Same body, same bits.
+template <bool kBatch>
+__global__ void __launch_bounds__(256) k_integrate(StepParams P0, const SysDesc* __restrict__ S,
+                                                   int nsys, Arrays A, CellList C, int n,
+                                                   DevCounters* ctrs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if constexpr (kBatch) {
+    const int sk = sys_of(S, nsys, (uint32_t)i);
+    integrate_body(S[sk].P, S[sk].cell_off, ctrs + sk, A, C, i);
+  } else {
+    integrate_body(P0, 0u, ctrs, A, C, i);
+  }
+}
+
+// Cell key only (set-up: particles loaded, nothing moves).
+__global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellList C, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int sk = sys_of(S, nsys, (uint32_t)i);
   const float4 p = A.pos[i];
-  const int c = cell_of(P, p.x, p.y, p.z);
+  const uint32_t c = S[sk].cell_off + (uint32_t)cell_of(S[sk].P, p.x, p.y, p.z);
   C.key[i] = (uint32_t)c;
   C.rank[i] = atomicAdd(&C.count[c], 1u);
 }
@@ -419,20 +435,28 @@ __global__ void k_unsort(Arrays A, int n, float4* out_pos, float4* out_vel, floa
   if (out_type) out_type[id] = is_solid(p.w) ? 1 : 0;
 }
 
-__global__ void k_bump_step(DevCounters* ctr) { ctr->step += 1u; }
+__global__ void k_bump_step(DevCounters* ctr, int nsys) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nsys) ctr[k].step += 1u;
+}
 
 // ---------------------------------------------------------------------------
 // Host launch wrappers.
 // ---------------------------------------------------------------------------
 static inline int blocks(long n, int t) { return (int)((n + t - 1) / t); }
 
-void launch_integrate(const StepParams& P, const Arrays& A, const CellList& C, int n,
-                      DevCounters* ctr, cudaStream_t s) {
-  if (n > 0) k_integrate<<<blocks(n, 256), 256, 0, s>>>(P, A, C, n, ctr);
+void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                      const CellList& C, int n, DevCounters* ctr, cudaStream_t s) {
+  if (n <= 0) return;
+  if (nsys == 1)
+    k_integrate<false><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr);
+  else
+    k_integrate<true><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr);
 }
 
-void launch_key(const StepParams& P, const Arrays& A, const CellList& C, int n, cudaStream_t s) {
-  if (n > 0) k_key<<<blocks(n, 256), 256, 0, s>>>(P, A, C, n);
+void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
+                cudaStream_t s) {
+  if (n > 0) k_key<<<blocks(n, 256), 256, 0, s>>>(S, nsys, A, C, n);
 }
 
 int scan_blocks(int ncells) { return blocks(ncells, kScanChunk); }
@@ -478,6 +502,8 @@ void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, flo
     k_unsort<<<blocks(n, 256), 256, 0, s>>>(A, n, out_pos, out_vel, out_frc, out_id, out_type);
 }
 
-void launch_bump_step(DevCounters* ctr, cudaStream_t s) { k_bump_step<<<1, 1, 0, s>>>(ctr); }
+void launch_bump_step(DevCounters* ctr, int nsys, cudaStream_t s) {
+  k_bump_step<<<blocks(nsys, 128), 128, 0, s>>>(ctr, nsys);
+}
 
 }  // namespace dpd

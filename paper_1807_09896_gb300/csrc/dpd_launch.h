@@ -5,15 +5,18 @@
 
 namespace dpd {
 
-void launch_integrate(const StepParams& P, const Arrays& A, const CellList& C, int n,
-                      DevCounters* ctr, cudaStream_t s);
-void launch_key(const StepParams& P, const Arrays& A, const CellList& C, int n, cudaStream_t s);
+// P0: parameters of system 0, used directly when nsys == 1.
+void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                      const CellList& C, int n, DevCounters* ctr, cudaStream_t s);
+void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
+                cudaStream_t s);
 int scan_blocks(int ncells);
 void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s);
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s);
-void launch_force(const StepParams& P, const Arrays& A, const uint32_t* start, int n,
-                  DevCounters* ctr, int kick, int variant, cudaStream_t s);
+void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                  const uint32_t* start, int n, DevCounters* ctr, int kick, int variant,
+                  cudaStream_t s);
 int force_variants();
 const char* force_variant_name(int v);
 void launch_profile(const float4* pos, const float4* vel, int n, int axis, int nbins, float lo,
@@ -25,7 +28,7 @@ void launch_load(const StepParams& P, const float4* in_pos, const float4* in_vel
                  cudaStream_t s);
 void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, float4* out_frc,
                    int* out_id, uint8_t* out_type, cudaStream_t s);
-void launch_bump_step(DevCounters* ctr, cudaStream_t s);
+void launch_bump_step(DevCounters* ctr, int nsys, cudaStream_t s);
 void set_global_error(const char* msg);
 
 }  // namespace dpd

@@ -1,0 +1,55 @@
+// dpd_system.h -- the handle behind dpd_t (internal; shared by the single-system
+// ABI and the batch ABI, which copies systems into one engine).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "dpd_common.cuh"
+#include "dpd_engine.h"
+
+struct dpd_system {
+  // parameters (DPD units)
+  double box[3] = {0, 0, 0};
+  double rho = 3.0;
+  double a[4] = {25, 25, 25, 25};
+  double gamma = 4.5, sigma = 3.0, kBT = 1.0, dt = 0.01;
+  double lambda = 0.65;
+  double g[3] = {0, 0, 0};
+  double vw[3] = {0, 0, 0};
+  double margin = 0.5;
+  uint64_t seed = 0;
+  uint32_t sys = 0;
+  int reflect_variant = 0;
+  int sample_every = 0;
+  int nc[3] = {0, 0, 0};
+  int ncells = 0;
+  // phase field and band mask (device)
+  float* d_phi = nullptr;
+  int pd[3] = {0, 0, 0};
+  double h = 0.0;
+  uint8_t* d_band = nullptr;
+  // particles: one-system engine
+  dpd::Engine E;
+  int n_fluid = 0;
+  bool loaded = false;
+  bool params_dirty = true;
+  uint64_t host_step = 0;
+  // staging for host reads
+  float4* d_out4 = nullptr;
+  int* d_out_id = nullptr;
+  uint8_t* d_out_type = nullptr;
+  int out_cap = 0;
+  // profile accumulators and diagnostics
+  double* d_prof = nullptr;
+  int prof_cap = 0, prof_axis = 2, prof_nbins = 0;
+  double prof_lo = 0, prof_hi = 0;
+  double* d_stats = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+};
+
+namespace dpd {
+// Kernel parameters of a system, from its host-side settings.
+StepParams make_params(const dpd_system* h);
+}  // namespace dpd

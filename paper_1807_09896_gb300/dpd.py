@@ -46,6 +46,18 @@ _SIGS = {
     "dpd_set_stream": (_i, [_vp, _vp]),
     "dpd_destroy": (_i, [_vp]),
     "dpd_last_error": (ctypes.c_char_p, [_vp]),
+    "dpd_batch_create": (_i, [ctypes.POINTER(_vp), _i, _vp]),
+    "dpd_batch_step": (_i, [_vp, _i]),
+    "dpd_batch_time_phases": (_i, [_vp, _i, _vp]),
+    "dpd_batch_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
+    "dpd_batch_get_state": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i]),
+    "dpd_batch_get_stats": (_i, [_vp, _i, _vp]),
+    "dpd_batch_set_option": (_i, [_vp, ctypes.c_char_p, _d]),
+    "dpd_batch_get_option": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_d)]),
+    "dpd_batch_num_particles": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "dpd_batch_set_stream": (_i, [_vp, _vp]),
+    "dpd_batch_destroy": (_i, [_vp]),
+    "dpd_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 _lib = None
@@ -278,6 +290,124 @@ class System:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batches -------------------------------------------------------------------
+
+def dpd_batch_last_error(hb) -> str:
+    return load_library().dpd_batch_last_error(hb).decode(errors="replace")
+
+
+def _bcheck(hb, rc):
+    if rc != DPD_OK:
+        raise DPDError(rc, dpd_batch_last_error(hb))
+    return rc
+
+
+def dpd_batch_create(handles):
+    """Batch of loaded systems (a list of dpd handles)."""
+    L = load_library()
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                             for h in handles])
+    hb = ctypes.c_void_p()
+    rc = L.dpd_batch_create(ctypes.byref(hb), len(handles), ctypes.cast(arr, ctypes.c_void_p))
+    if rc != DPD_OK:
+        raise DPDError(rc, L.dpd_batch_last_error(None).decode(errors="replace"))
+    return hb
+
+
+def dpd_batch_step(hb, nsteps: int):
+    return _bcheck(hb, load_library().dpd_batch_step(hb, int(nsteps)))
+
+
+def dpd_batch_time_phases(hb, nsteps: int) -> dict:
+    ms = np.zeros(len(PHASES), np.float64)
+    _bcheck(hb, load_library().dpd_batch_time_phases(hb, int(nsteps), _ptr(ms)))
+    return dict(zip(PHASES, ms.tolist()))
+
+
+def dpd_batch_autotune(hb, nsteps: int = 5):
+    nv = int(dpd_batch_get_option(hb, "force_variants"))
+    ms = np.zeros(nv, np.float64)
+    chosen = ctypes.c_int()
+    _bcheck(hb, load_library().dpd_batch_autotune(hb, int(nsteps), _ptr(ms), ctypes.byref(chosen)))
+    return chosen.value, ms.tolist()
+
+
+def dpd_batch_num_particles(hb, k: int):
+    n, nf = ctypes.c_int(), ctypes.c_int()
+    _bcheck(hb, load_library().dpd_batch_num_particles(hb, int(k), ctypes.byref(n), ctypes.byref(nf)))
+    return n.value, nf.value
+
+
+def dpd_batch_get_state(hb, k: int, pos4=None, vel4=None, force4=None, ids=None, types=None,
+                        where=DPD_HOST):
+    if where == DPD_HOST and all(x is None for x in (pos4, vel4, force4, ids, types)):
+        n, _ = dpd_batch_num_particles(hb, k)
+        pos4 = np.zeros((n, 4), np.float32)
+        vel4 = np.zeros((n, 4), np.float32)
+        force4 = np.zeros((n, 4), np.float32)
+        ids = np.zeros(n, np.int32)
+        types = np.zeros(n, np.uint8)
+    _bcheck(hb, load_library().dpd_batch_get_state(hb, int(k), _ptr(pos4), _ptr(vel4), _ptr(force4),
+                                                   _ptr(ids), _ptr(types), where))
+    return pos4, vel4, force4, ids, types
+
+
+def dpd_batch_get_stats(hb, k: int) -> np.ndarray:
+    out = np.zeros(8, np.float64)
+    _bcheck(hb, load_library().dpd_batch_get_stats(hb, int(k), _ptr(out)))
+    return out
+
+
+def dpd_batch_set_option(hb, key: str, value: float):
+    return _bcheck(hb, load_library().dpd_batch_set_option(hb, key.encode(), float(value)))
+
+
+def dpd_batch_get_option(hb, key: str) -> float:
+    v = ctypes.c_double()
+    _bcheck(hb, load_library().dpd_batch_get_option(hb, key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def dpd_batch_set_stream(hb, stream):
+    s = getattr(stream, "cuda_stream", stream)
+    return _bcheck(hb, load_library().dpd_batch_set_stream(hb, ctypes.c_void_p(s) if s else None))
+
+
+def dpd_batch_destroy(hb):
+    if hb:
+        load_library().dpd_batch_destroy(hb)
+
+
+class Batch:
+    """Owns one batch handle built from loaded Systems (which must outlive it)."""
+
+    def __init__(self, systems, **options):
+        self.systems = list(systems)
+        self.hb = dpd_batch_create([s.h for s in self.systems])
+        for k, v in options.items():
+            dpd_batch_set_option(self.hb, k, v)
+
+    def step(self, n=1):
+        return dpd_batch_step(self.hb, n)
+
+    def state(self, k):
+        return dpd_batch_get_state(self.hb, k)
+
+    def stats(self, k):
+        return dpd_batch_get_stats(self.hb, k)
+
+    def close(self):
+        if self.hb:
+            dpd_batch_destroy(self.hb)
+            self.hb = None
 
     def __del__(self):
         try:

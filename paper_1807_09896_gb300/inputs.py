@@ -192,6 +192,36 @@ def sphere_pack(L: float, nspheres: int, rmin: float, rmax: float, rho: float = 
     chunk = 1 << 18
     for s in range(0, ncand, chunk):
         d[s:s + chunk] = _sphere_distance(cand[s:s + chunk], cs, rs, L)
-    fpos = cand[d > 0]
+    # A thin shell 0 < d <= 0.02 r_c next to the curved surfaces stays empty: there the
+    # grid-interpolated phase field can fall a little below zero (interpolation error
+    # ~ h^2/8 |phi''| ~ 0.012 in phi, ~ 0.009 r_c in distance), and a fluid particle
+    # must start on the fluid side of the sharp interface.
+    fpos = cand[d > 0.02]
     spos = cand[(d <= 0) & (d >= -layer)]
     return _finish(f"spheres_{L:g}_{nspheres}", box, phi, h, fpos, spos, kBT, rng)
+
+
+def ensemble(nsys: int = 64, seed: int = 0, min_fluid: int = 2000, max_fluid: int = 60000,
+             edge=(8, 40), gap=(6, 30)):
+    """Independent systems of uneven sizes: alternately plane channels (box edges
+    and gap widths drawn from `edge` and `gap`) and periodic sphere-pack pores,
+    with seeds seed + k and fluid counts kept within [min_fluid, max_fluid]."""
+    rng = np.random.default_rng(1_000_003 + seed)
+    out = []
+    k = 0
+    while len(out) < nsys:
+        s = seed + k
+        k += 1
+        if len(out) % 2 == 0:
+            H = float(rng.integers(gap[0], gap[1] + 1))
+            target = rng.uniform(min_fluid, max_fluid) / (3.0 * H)
+            side = max(float(edge[0]), min(float(edge[1]), round(math.sqrt(target))))
+            Ly = max(float(edge[0]), min(float(edge[1]), round(target / side)))
+            w = channel(side, Ly, H, seed=s)
+        else:
+            L = float(rng.integers(max(edge[0], 10), min(edge[1], 26) + 1))
+            nsph = int(rng.integers(2, 6))
+            w = sphere_pack(L, nsph, 0.12 * L, 0.22 * L, seed=s)
+        if min_fluid <= w.n_fluid <= max_fluid:
+            out.append(w)
+    return out

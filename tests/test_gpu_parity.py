@@ -52,6 +52,7 @@ CASES = {
     "bulk_3cube": lambda: inputs.bulk(3.0, seed=1),
     "bulk_no_walls": lambda: inputs.bulk((4.0, 5.0, 6.0), seed=2),
     "channel_tiles": lambda: inputs.channel(24.0, 16.0, 12.0, seed=4),
+    "sphere_pack": lambda: inputs.sphere_pack(12.0, 3, 2.0, 3.0, seed=5),
 }
 
 
