@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel_1m", choices=["channel_1m", "channel_200k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -232,6 +234,53 @@ def run_reference(args):
     return 0
 
 
+def measure_batched(dpd, torch, dev, stream, rank, nsys=64, steps=200):
+    """Ensemble of 64 uneven channels and sphere-pack pores (2k-60k fluid particles
+    each): the batch (one launch per phase over all systems, graph replay) against
+    the same systems stepped one after another, each with its own graphs."""
+    from paper_1807_09896_gb300 import inputs
+
+    ws = inputs.ensemble(nsys, seed=64 * rank)
+    systems = []
+    for k, w in enumerate(ws):
+        gx = 0.01 if w.gap else 0.005
+        s = dpd.System.from_workload(w, g=(gx, 0.0, 0.0), seed=k, system=k)
+        dpd.dpd_set_stream(s.h, stream)
+        systems.append(s)
+    nf = sum(w.n_fluid for w in ws)
+    b = dpd.Batch(systems, graph_steps=20)
+    dpd.dpd_batch_set_stream(b.hb, stream)
+    chosen, _ = dpd.dpd_batch_autotune(b.hb, 3)
+    b.step(20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_b = e0.elapsed_time(e1)
+    for s in systems:
+        s.set_option("use_graph", 1)
+        s.set_option("graph_steps", 20)
+        s.step(20)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for s in systems:
+        s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_s = e0.elapsed_time(e1)
+    b.close()
+    for s in systems:
+        s.close()
+    return {"workload": f"{nsys} systems (alternating plane channels and sphere-pack pores, "
+                        f"2k-60k fluid each, {nf} fluid in total)",
+            "steps": steps, "value": nf * steps / (ms_b / 1e3), "unit": "particle-steps/s",
+            "serial_value": nf * steps / (ms_s / 1e3), "speedup_vs_serial": ms_s / ms_b,
+            "ms_per_step_batched": ms_b / steps, "ms_per_step_serial": ms_s / steps,
+            "force_launch_shape": chosen}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -339,6 +388,9 @@ def run_ours(args):
     st = s.stats()
     s.close()
 
+    batched = None if args.no_batched else measure_batched(dpd, torch, dev, stream, rank,
+                                                            steps=args.batched_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(args.workload, budget_s=10.0)
@@ -378,6 +430,7 @@ def run_ours(args):
             "clocks": ck,
             "cpu_baseline": cpu,
             "diagnostics": {"reflections": st[5], "fallbacks": st[6]},
+            "batched": batched,
         }
         print(json.dumps(line))
     if world > 1:

@@ -184,7 +184,8 @@ int dpd_get_stats(dpd_t* h, double out[8]);
 /* Set or read a named option: "lambda", "band_margin", "reflect_variant" (0:
  * displacement of the step, 1: v(t) dt as printed in Eq. 17), "seed" (integer
  * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "sample_every",
- * "step" (the step counter, part of the noise counter), "use_graph" (1: replay
+ * "a_ff", "a_fs", "gamma", "sigma", "g_x", "g_y", "g_z" (the create-time
+ * parameters), "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
  * default 20), "force_variant" (launch shape of the pair-force kernel, see
  * dpd_autotune).  Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
@@ -194,6 +195,33 @@ int dpd_get_option(dpd_t* h, const char* key, double* value);
 
 /* Particle counts currently loaded. */
 int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
+
+/* Reverse-mode gradient of a near-wall velocity-profile loss over a window of
+ * nsteps time steps, with respect to (a_fs, gamma, g_x).  The paper has no
+ * counterpart (it sets a_fs, gamma and g by hand); this calibrates the wall
+ * interaction of Eqs. 4-10 and the body force of Sec. III.A against a target
+ * profile.
+ * Window: f(0) is recomputed at the current state with the current parameters
+ * and predicted velocity v(0); then nsteps steps run exactly as dpd_step (the
+ * system ends the call advanced by nsteps, its statistics counted once).
+ * Loss: fluid particles are binned by their distance to the nearer wall,
+ * d = min(x_axis - wall_lo, wall_hi - x_axis), into nbins bins of width
+ * bin_width (binary32 decision); u_b is the mean x velocity of bin b over the
+ * states after steps 1..nsteps; L = sum_b (u_b - target[b])^2 (bins never
+ * visited are skipped).
+ * Gradient: the discrete adjoint of every step (pair force with the noise drawn
+ * again from its counter, drift, predicted velocity, closing kick, and Eq. 17
+ * reflection including the gradient of the interpolated phase field).  Events
+ * are frozen: reflection decisions, cell lists and bin membership are those of
+ * the forward trajectory.  tie_sigma = 1 keeps sigma = sqrt(2 gamma kBT) (Eq. 8)
+ * so d/dgamma includes the random force; 0 holds sigma fixed.  grad[3] receives
+ * dL/da_fs, dL/dgamma, dL/dg_x; loss_out (may be NULL) receives L.
+ * Memory: a checkpoint every ckpt_every steps (nsteps must be a multiple) and a
+ * record of ckpt_every steps; the backward pass recomputes one segment at a
+ * time.  Requires reflect_variant 0. */
+int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
+                       double wall_hi, int nbins, double bin_width, const double* target,
+                       int tie_sigma, double* loss_out, double grad[3]);
 
 /* ---- Batches: many independent systems advanced together ------------------
  * The paper has no counterpart (it runs one system at a time); this is the

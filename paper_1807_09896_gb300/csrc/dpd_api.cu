@@ -435,6 +435,18 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
   h->params_dirty = true;
   if (k == "lambda") {
     h->lambda = v;
+  } else if (k == "a_ff") {
+    h->a[0] = v;
+  } else if (k == "a_fs") {
+    h->a[1] = h->a[2] = v;
+  } else if (k == "gamma") {
+    if (v < 0) return fail(h, DPD_EINVAL, "gamma must be >= 0");
+    h->gamma = v;
+  } else if (k == "sigma") {
+    if (v < 0) return fail(h, DPD_EINVAL, "sigma must be >= 0");
+    h->sigma = v;
+  } else if (k == "g_x" || k == "g_y" || k == "g_z") {
+    h->g[k.back() - 'x'] = v;
   } else if (k == "band_margin") {
     if (!(v > 0.0) || v > 1.0) return fail(h, DPD_EINVAL, "band_margin must be in (0, 1]");
     h->margin = v;
@@ -486,6 +498,13 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   const std::string k(key);
   const dpd::Engine& E = h->E;
   if (k == "lambda") *v = h->lambda;
+  else if (k == "a_ff") *v = h->a[0];
+  else if (k == "a_fs") *v = h->a[1];
+  else if (k == "gamma") *v = h->gamma;
+  else if (k == "sigma") *v = h->sigma;
+  else if (k == "kBT") *v = h->kBT;
+  else if (k == "dt") *v = h->dt;
+  else if (k == "g_x" || k == "g_y" || k == "g_z") *v = h->g[k.back() - 'x'];
   else if (k == "band_margin") *v = h->margin;
   else if (k == "reflect_variant") *v = h->reflect_variant;
   else if (k == "seed") *v = (double)h->seed;

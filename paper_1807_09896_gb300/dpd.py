@@ -37,6 +37,7 @@ _SIGS = {
     "dpd_time_phases": (_i, [_vp, _i, _vp]),
     "dpd_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
     "dpd_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
+    "dpd_adjoint_window": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, _vp, _i, _vp, _vp]),
     "dpd_velocity_profile": (_i, [_vp, _i, _i, _d, _d, _vp, _i]),
     "dpd_velocity_profile_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _vp, _i, _vp]),
     "dpd_get_stats": (_i, [_vp, _vp]),
@@ -164,6 +165,20 @@ def dpd_autotune(h, nsteps: int = 5):
     chosen = ctypes.c_int()
     _check(h, load_library().dpd_autotune(h, int(nsteps), _ptr(ms), ctypes.byref(chosen)))
     return chosen.value, ms.tolist()
+
+
+def dpd_adjoint_window(h, nsteps, ckpt_every, axis, wall_lo, wall_hi, target, bin_width,
+                       tie_sigma=True):
+    """Loss and gradient (dL/da_fs, dL/dgamma, dL/dg_x) of the near-wall profile loss
+    over a window of nsteps steps (see include/dpd.h)."""
+    t = np.ascontiguousarray(target, np.float64)
+    grad = np.zeros(3, np.float64)
+    loss = np.zeros(1, np.float64)
+    _check(h, load_library().dpd_adjoint_window(h, int(nsteps), int(ckpt_every), int(axis),
+                                                float(wall_lo), float(wall_hi), len(t),
+                                                float(bin_width), _ptr(t), int(bool(tie_sigma)),
+                                                _ptr(loss), _ptr(grad)))
+    return float(loss[0]), grad
 
 
 def dpd_num_particles(h):
