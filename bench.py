@@ -60,6 +60,7 @@ def _args():
     ap.add_argument("--workload", default="channel_1m", choices=["channel_1m", "channel_200k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip adjoint and precision lines")
     ap.add_argument("--batched-steps", type=int, default=200)
     return ap.parse_args()
 
@@ -281,6 +282,82 @@ def measure_batched(dpd, torch, dev, stream, rank, nsys=64, steps=200):
             "force_launch_shape": chosen}
 
 
+def measure_adjoint(dpd, torch, dev, stream, nsteps=200, ckpt=20):
+    """Adjoint window vs forward steps on the calibration channel 32 x 16 x 16
+    (~25k fluid particles): the same 200 steps plain (graph replay) and with the
+    near-wall loss gradient (forward + checkpointed recompute + reverse)."""
+    from paper_1807_09896_gb300 import adjoint, inputs
+
+    w = inputs.channel(32.0, 16.0, 16.0, seed=0)
+    s = dpd.System.from_workload(w, g=(0.02, 0.0, 0.0))
+    dpd.dpd_set_stream(s.h, stream)
+    target = adjoint.poiseuille_wall_target(16.0, 0.02, 3.0, 0.9, 8, 0.25)
+    loss = adjoint.NearWallLoss(0.0, 16.0, target)
+    theta = (25.0, 4.5, 0.02)
+    adjoint.window_loss_and_grad(s, theta, loss, nsteps, ckpt)  # warm-up
+    s.step(nsteps)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.step(nsteps)
+    torch.cuda.synchronize(dev)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L, g = adjoint.window_loss_and_grad(s, theta, loss, nsteps, ckpt)
+    torch.cuda.synchronize(dev)
+    t_adj = time.perf_counter() - t0
+    s.close()
+    return {"workload": f"channel 32x16x16 (gap 16), {w.n_fluid} fluid, {nsteps}-step window, "
+                        f"checkpoint every {ckpt}",
+            "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj, "adjoint_over_forward": t_adj / t_fwd,
+            "loss": L, "grad_a_fs_gamma_gx": [float(x) for x in g]}
+
+
+def measure_precision(dpd, nsteps=100):
+    """Binary32 GPU against the binary64 oracle from identical state on the
+    10 x 10 x 10-gap channel: one step (force, position, velocity errors) and the
+    divergence of the two trajectories over nsteps steps."""
+    import numpy as np
+
+    import oracle
+    from paper_1807_09896_gb300 import inputs
+
+    w = inputs.channel(10.0, 10.0, 10.0, seed=0)
+    p = oracle.Params(box=w.box, g=(0.02, 0.0, 0.0), seed=0)
+    s = dpd.System.from_workload(w, g=(0.02, 0.0, 0.0))
+    field = oracle.Field(w.phi, w.h)
+    pos4, vel4, f4, ids, types = s.state()
+    st = oracle.State(pos4[:, :3].astype(np.float64), vel4[:, :3].astype(np.float64),
+                      f4[:, :3].astype(np.float64), ids, types, 0)
+    fluid = types == 0
+    s.step(1)
+    g1 = s.state()
+    o1 = oracle.step(st, p, field)
+    scale = np.abs(o1.frc[fluid]).max()
+    ferr = float(np.abs(g1[2][fluid, :3] - o1.frc[fluid]).max() / scale)
+    L = np.asarray(w.box)
+    dp = g1[0][:, :3] - o1.pos
+    dp -= L * np.round(dp / L)
+    perr = float(np.abs(dp).max())
+    verr = float(np.abs(g1[1][fluid, :3] - o1.vel[fluid]).max())
+    o = o1
+    div = {}
+    for k in range(2, nsteps + 1):
+        s.step(1)
+        o = oracle.step(o, p, field)
+        if k in (10, 30, 100):
+            g = s.state()
+            d = g[0][:, :3] - o.pos
+            d -= L * np.round(d / L)
+            div[str(k)] = {"rms_position": float(np.sqrt((d[fluid] ** 2).sum(1).mean())),
+                           "rms_velocity": float(np.sqrt(((g[1][fluid, :3] - o.vel[fluid]) ** 2).sum(1).mean()))}
+    s.close()
+    return {"workload": f"channel 10x10x10 gap, {w.n_fluid} fluid + {w.n_solid} solid",
+            "one_step": {"force_max_err_over_max_force": ferr, "position_max_abs": perr,
+                         "velocity_max_abs": verr},
+            "trajectory_divergence": div,
+            "note": "FP32 force/integrate, FP64 sums; trajectories of a chaotic system diverge"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -390,6 +467,8 @@ def run_ours(args):
 
     batched = None if args.no_batched else measure_batched(dpd, torch, dev, stream, rank,
                                                             steps=args.batched_steps)
+    adj = None if args.no_extras else measure_adjoint(dpd, torch, dev, stream)
+    precision = None if (args.no_extras or rank != 0) else measure_precision(dpd)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -431,6 +510,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "diagnostics": {"reflections": st[5], "fallbacks": st[6]},
             "batched": batched,
+            "adjoint": adj,
+            "fp32_vs_fp64": precision,
         }
         print(json.dumps(line))
     if world > 1:

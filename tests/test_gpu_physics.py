@@ -1,0 +1,109 @@
+"""Statistical properties the method must reproduce, run on the GPU through the C ABI.
+
+* Eq. 8 thermostat: a periodic fluid settles at k_BT (Sec. III.A: deviations measure
+  integration error).
+* No-slip Poiseuille flow (Sec. III.A, Eqs. 18-19): the steady profile of a channel
+  driven by g_x is a parabola vanishing at the phi = 0 walls (slip length ~ 0), its
+  mean is 2/3 of its maximum, density and temperature are flat away from the walls,
+  and no fluid particle is ever found at phi < 0.
+* Complex geometry: no penetration into a sphere pack over a long run.
+The absolute viscosity of the 3-D fluid is not pinned by the paper (it prints 2-D
+values only); the fitted value is reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_09896_gb300 import dpd, inputs
+from parity_helpers import gpu_state, make_system, params_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_09896_gb300 import _build
+
+    _build.build()
+
+
+@pytest.mark.parametrize("kBT", [1.0, 0.5])
+def test_thermostat_holds_the_temperature(kBT):
+    w = inputs.bulk(10.0, seed=5, kBT=kBT)
+    p = params_for(w, seed=9, kBT=kBT, sigma=math.sqrt(2 * 4.5 * kBT))
+    s = make_system(w, p)
+    s.step(1000)
+    temps = []
+    for _ in range(200):
+        s.step(10)
+        st = s.stats()
+        n = st[4]
+        mom = st[:3] / n
+        temps.append((st[3] / n - (mom ** 2).sum()) / 3.0)
+    T = float(np.mean(temps))
+    print(f"kBT {kBT}: measured {T:.4f}")
+    assert abs(T / kBT - 1.0) < 0.02, T
+    s.close()
+
+
+def test_poiseuille_flow_has_no_slip_at_the_phase_field_walls():
+    H, g, rho, mu_guess = 10.0, 0.02, 3.0, 0.9
+    w = inputs.channel(10.0, 10.0, H, seed=7)
+    # start near the expected profile to shorten the transient
+    z = w.pos[:, 2].astype(np.float64)
+    fluid = w.type == 0
+    w.vel[fluid, 0] += (rho * g * z * (H - z) / (2 * mu_guess))[fluid].astype(np.float32)
+    p = params_for(w, g=(g, 0.0, 0.0), seed=3)
+    s = make_system(w, p)
+    field = oracle.Field(w.phi, w.h)
+    s.step(4000)
+    nb = 40
+    s.profile(2, nb, 0.0, H, mode=3)
+    s.set_option("sample_every", 5)
+    for _ in range(6):
+        s.step(2000)
+        pos, _, _, types = gpu_state(s)
+        assert oracle.phi_many(field, pos[types == 0]).min() >= 0.0  # no penetration
+    prof = s.profile(2, nb, 0.0, H, mode=2)
+    cnt = prof[:, 0]
+    u = prof[:, 1] / cnt
+    zc = (np.arange(nb) + 0.5) * H / nb
+    inner = (zc > 1.0) & (zc < H - 1.0)
+    c2, c1, c0 = np.polyfit(zc[inner], u[inner], 2)
+    roots = np.sort(np.roots([c2, c1, c0]).real)
+    slip_lo, slip_hi = -roots[0], roots[1] - H  # positive: the zero lies inside the solid
+    mu = -rho * g / (2 * c2)
+    ubar = (prof[:, 1].sum()) / cnt.sum()
+    umax = c0 - c1 * c1 / (4 * c2)
+    dens = cnt / cnt[inner].mean()
+    temp = (prof[:, 4] / cnt - (prof[:, 1:4] / cnt[:, None]) ** 2 @ np.ones(3)) / 3.0
+    print(f"Poiseuille: mu = {mu:.4f}, slip lengths {slip_lo:.3f} / {slip_hi:.3f}, "
+          f"mean/max = {ubar / umax:.4f}, density flat to {np.abs(dens[inner] - 1).max():.3f}, "
+          f"T in [{temp[inner].min():.3f}, {temp[inner].max():.3f}], "
+          f"fallbacks {s.stats()[6]:.0f} of {s.stats()[5]:.0f} reflections")
+    assert abs(slip_lo) < 0.25 and abs(slip_hi) < 0.25
+    assert abs(ubar / umax - 2.0 / 3.0) < 0.03
+    assert np.abs(dens[inner] - 1).max() < 0.05
+    assert np.abs(temp[inner] - 1).max() < 0.05
+    assert 0.5 < mu < 1.5
+    s.close()
+
+
+def test_no_penetration_into_a_sphere_pack():
+    w = inputs.sphere_pack(16.0, 4, 2.5, 4.0, seed=12)
+    p = params_for(w, g=(0.05, 0.0, 0.0), seed=2)
+    s = make_system(w, p)
+    field = oracle.Field(w.phi, w.h)
+    for _ in range(5):
+        s.step(400)
+        pos, _, _, types = gpu_state(s)
+        assert oracle.phi_many(field, pos[types == 0]).min() >= 0.0
+    st = s.stats()
+    assert st[5] > 0 and st[6] <= 0.01 * st[5]
+    s.close()
