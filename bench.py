@@ -72,6 +72,21 @@ WORKLOADS = {
 }
 
 
+def reduce_over_ranks(ms: float, units: float, device=None):
+    """Whole-job timing across ranks: the slowest rank's time and the total work.
+    Single process: returned unchanged."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _workload(name, seed):
     from paper_1807_09896_gb300 import inputs
 
@@ -415,11 +430,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
     launches = int(s.get_option("kernel_launches") - launches0)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.n_fluid * args.steps / (ms / 1e3)
+    ms, units = reduce_over_ranks(ms, float(w.n_fluid) * args.steps, device=dev)
+    value = units / (ms / 1e3)
 
     # phase durations with CUDA events on the library's stream (same launches, no graph)
     nph = min(args.steps, 50)
@@ -455,11 +467,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = world * w.n_fluid * args.steps / e2e_s
+    e2e_s, e2e_units = reduce_over_ranks(e2e_s, float(w.n_fluid) * args.steps, device=dev)
+    e2e = e2e_units / e2e_s
     h2d = w.n * (16 + 16 + 4 + 1)
     d2h = w.n * (16 * 3 + 4 + 1) + nb * 5 * 8
     st = s.stats()
