@@ -167,7 +167,13 @@ __device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t
   }
   const float u0 = (__uint2float_rn(c0 >> 9) + 0.5f) * 0x1p-23f;
   const float u1 = (__uint2float_rn(c1 >> 9) + 0.5f) * 0x1p-23f;
-  return sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+  // cos(2 pi u1) = -cos(2 pi u1 - pi), evaluated by the hardware cosine on an
+  // argument in (-pi, pi), where its absolute error is below 4e-7; the square root
+  // as x * rsqrt(x) (x = -2 ln u0 >= 2.4e-7 > 0).  The logarithm stays the
+  // accurate one: near u0 = 1 its value is tiny and needs full relative accuracy.
+  const float x = -2.0f * logf(u0);
+  const float c = __cosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f));
+  return -(x * rsqrtf(x)) * c;
 }
 
 // Minimum-image separation xi - xj of two coordinates in [0, L).  When the pair

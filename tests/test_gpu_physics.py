@@ -53,8 +53,11 @@ def test_thermostat_holds_the_temperature(kBT):
 
 
 def test_poiseuille_flow_has_no_slip_at_the_phase_field_walls():
-    H, g, rho, mu_guess = 10.0, 0.02, 3.0, 0.9
-    w = inputs.channel(10.0, 10.0, H, seed=7)
+    """Channel 20 x 20, gap 10, g = 0.02.  Over six seeds the fitted zero of the
+    profile lies 0.10 +- 0.04 r_c inside the solid at either wall (1% of the gap)
+    and mu = 0.84 +- 0.02; the bounds below sit at about 5 standard deviations."""
+    H, g, rho, mu_guess = 10.0, 0.02, 3.0, 0.84
+    w = inputs.channel(20.0, 20.0, H, seed=7)
     # start near the expected profile to shorten the transient
     z = w.pos[:, 2].astype(np.float64)
     fluid = w.type == 0
@@ -62,12 +65,12 @@ def test_poiseuille_flow_has_no_slip_at_the_phase_field_walls():
     p = params_for(w, g=(g, 0.0, 0.0), seed=3)
     s = make_system(w, p)
     field = oracle.Field(w.phi, w.h)
-    s.step(4000)
+    s.step(10000)
     nb = 40
     s.profile(2, nb, 0.0, H, mode=3)
     s.set_option("sample_every", 5)
-    for _ in range(6):
-        s.step(2000)
+    for _ in range(4):
+        s.step(5000)
         pos, _, _, types = gpu_state(s)
         assert oracle.phi_many(field, pos[types == 0]).min() >= 0.0  # no penetration
     prof = s.profile(2, nb, 0.0, H, mode=2)
@@ -87,11 +90,12 @@ def test_poiseuille_flow_has_no_slip_at_the_phase_field_walls():
           f"mean/max = {ubar / umax:.4f}, density flat to {np.abs(dens[inner] - 1).max():.3f}, "
           f"T in [{temp[inner].min():.3f}, {temp[inner].max():.3f}], "
           f"fallbacks {s.stats()[6]:.0f} of {s.stats()[5]:.0f} reflections")
-    assert abs(slip_lo) < 0.25 and abs(slip_hi) < 0.25
+    assert abs(0.5 * (slip_lo + slip_hi)) < 0.2
+    assert abs(slip_lo) < 0.3 and abs(slip_hi) < 0.3
     assert abs(ubar / umax - 2.0 / 3.0) < 0.03
     assert np.abs(dens[inner] - 1).max() < 0.05
     assert np.abs(temp[inner] - 1).max() < 0.05
-    assert 0.5 < mu < 1.5
+    assert 0.7 < mu < 1.0
     s.close()
 
 
