@@ -82,13 +82,23 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
         ++seg;
         continue;
       }
-      const float4 pj = __ldg(&pos[j]);
-      const float dx = tx - (pj.x - sx);
-      const float dy = ty - (pj.y - sy);
-      const float dz = tz - (pj.z - sz);
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (r2 < 1.0f && r2 > 0.0f) list[cnt++][threadIdx.x] = (int)j;
-      ++j;
+      // up to four candidates per round, their loads issued together
+      const uint32_t m = min(min(e - j, 4u), (uint32_t)(kListCap - cnt));
+      float4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < (int)m) q[u] = __ldg(&pos[j + u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < (int)m) {
+          const float dx = tx - (q[u].x - sx);
+          const float dy = ty - (q[u].y - sy);
+          const float dz = tz - (q[u].z - sz);
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < 1.0f && r2 > 0.0f) list[cnt++][threadIdx.x] = (int)(j + u);
+        }
+      }
+      j += m;
     }
     // evaluate the listed pairs
 #pragma unroll kUnroll
