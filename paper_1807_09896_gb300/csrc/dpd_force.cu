@@ -28,7 +28,9 @@ namespace dpd {
 template <int kForceThreads, int kListCap, int kUnroll>
 __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* __restrict__ start,
                                            DevCounters* ctr, const Arrays& A, int i, float4 pi,
-                                           int (*list)[kForceThreads], int kick) {
+                                           int (*list)[kForceThreads],
+                                           uint32_t (*seg_b)[kForceThreads],
+                                           uint32_t (*seg_e)[kForceThreads], int kick) {
   const float4 vti = A.vt[i];
   const uint32_t idi = id_of(pi.w);
   const uint32_t step = ctr->step;
@@ -52,6 +54,18 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
   const bool inner = cx > 0 && cx < ncx - 1;
   const int nseg = inner ? 9 : 27;
+  if (inner) {
+    // the nine row ranges' cell starts, loaded together up front
+#pragma unroll
+    for (int rowi = 0; rowi < 9; ++rowi) {
+      int y = cy + rowi % 3 - 1, z = cz + rowi / 3 - 1;
+      y = y < 0 ? y + ncy : (y >= ncy ? y - ncy : y);
+      z = z < 0 ? z + ncz : (z >= ncz ? z - ncz : z);
+      const int row = (z * ncy + y) * ncx;
+      seg_b[rowi][threadIdx.x] = __ldg(&start[row + cx - 1]);
+      seg_e[rowi][threadIdx.x] = __ldg(&start[row + cx + 2]);
+    }
+  }
   int seg = 0;
   uint32_t j = 0, e = 0;
   float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
@@ -69,8 +83,8 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
         if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
         const int row = (z * ncy + y) * ncx;
         if (inner) {
-          j = __ldg(&start[row + cx - 1]);
-          e = __ldg(&start[row + cx + 2]);
+          j = seg_b[rowi][threadIdx.x];
+          e = seg_e[rowi][threadIdx.x];
           tx = pi.x; sx = 0.f;
         } else {
           int x = cx + part - 1;
@@ -155,6 +169,7 @@ __global__ void __launch_bounds__(kForceThreads, kMinBlocks)
 k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
         const uint32_t* __restrict__ start_all, int n, DevCounters* ctrs, int kick) {
   __shared__ int list[kListCap][kForceThreads];
+  __shared__ uint32_t seg_b[9][kForceThreads], seg_e[9][kForceThreads];
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
   if (i >= n) return;
   const float4 pi = A.pos[i];
@@ -162,9 +177,10 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
     force_body<kForceThreads, kListCap, kUnroll>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk, A,
-                                                 i, pi, list, kick);
+                                                 i, pi, list, seg_b, seg_e, kick);
   } else {
-    force_body<kForceThreads, kListCap, kUnroll>(P0, start_all, ctrs, A, i, pi, list, kick);
+    force_body<kForceThreads, kListCap, kUnroll>(P0, start_all, ctrs, A, i, pi, list, seg_b, seg_e,
+                                                 kick);
   }
 }
 
