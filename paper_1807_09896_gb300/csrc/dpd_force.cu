@@ -25,6 +25,50 @@ namespace dpd {
 // blocks per SM, unroll of the pair loop).  Every shape sums the same pairs in
 // the same order, so all of them give bit-identical forces; dpd_autotune picks
 // the fastest on the device at hand.
+// One pair term of Eq. 2 (Eqs. 3-10) for the separation d = r_i - r_j (|d| < r_c):
+// returns (m, e_x, e_y, e_z) with f_ij = m e, e = d / r, w = 1 - r and
+//   m = w (a_ij - gamma w (e . (vt_i - vt_j)) + sigma xi_ij / sqrt(dt)).
+// Every force kernel evaluates pairs through this function, so they agree bit for bit.
+__device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float dy, float dz,
+                                            float4 vti, const float4* __restrict__ vt, int jj,
+                                            float tagj, uint32_t idi, uint32_t step) {
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float inv_r = rsqrtf(r2);
+  const float r = r2 * inv_r;
+  const float w = 1.0f - r;
+  const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+  float vjx, vjy, vjz, a;
+  if (is_solid(tagj)) {
+    vjx = P.vw[0]; vjy = P.vw[1]; vjz = P.vw[2];
+    a = P.a_fs;
+  } else {
+    const float4 vtj = __ldg(&vt[jj]);
+    vjx = vtj.x; vjy = vtj.y; vjz = vtj.z;
+    a = P.a_ff;
+  }
+  const float ev = ex * (vti.x - vjx) + ey * (vti.y - vjy) + ez * (vti.z - vjz);
+  const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
+  const float mag = w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi);
+  return make_float4(mag, ex, ey, ez);
+}
+
+// Store the new pair force of target i and apply the closing half-kick
+// v(t+dt) = v(t) + dt/2 (F(t) + F(t+dt)), F = f + g (not for reflected particles).
+__device__ __forceinline__ void finish_target(const StepParams& P, const Arrays& A, int i, float4 vti,
+                                              float fx, float fy, float fz, DevCounters* ctr,
+                                              int kick) {
+  const float4 f_old = A.frc[i];
+  A.frc[i] = make_float4(fx, fy, fz, 0.0f);
+  if (kick && vti.w == 0.0f) {
+    float4 v = A.vel[i];
+    v.x = fmaf(P.half_dt, (f_old.x + fx) + 2.0f * P.g[0], v.x);
+    v.y = fmaf(P.half_dt, (f_old.y + fy) + 2.0f * P.g[1], v.y);
+    v.z = fmaf(P.half_dt, (f_old.z + fz) + 2.0f * P.g[2], v.z);
+    A.vel[i] = v;
+  }
+  if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&ctr->status, ST_NAN);
+}
+
 template <int kForceThreads, int kListCap, int kUnroll>
 __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* __restrict__ start,
                                            DevCounters* ctr, const Arrays& A, int i, float4 pi,
@@ -122,43 +166,16 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
       const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
       const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float inv_r = rsqrtf(r2);
-      const float r = r2 * inv_r;
-      const float w = 1.0f - r;
-      const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-      float vjx, vjy, vjz, a;
-      if (is_solid(pj.w)) {
-        vjx = P.vw[0]; vjy = P.vw[1]; vjz = P.vw[2];
-        a = P.a_fs;
-      } else {
-        const float4 vtj = __ldg(&vt[jj]);
-        vjx = vtj.x; vjy = vtj.y; vjz = vtj.z;
-        a = P.a_ff;
-      }
-      const float ev = ex * (vti.x - vjx) + ey * (vti.y - vjy) + ez * (vti.z - vjz);
-      const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.seed_lo, P.seed_hi);
-      const float mag = w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi);
-      fx = fmaf(mag, ex, fx);
-      fy = fmaf(mag, ey, fy);
-      fz = fmaf(mag, ez, fz);
+      const float4 t = pair_term(P, dx, dy, dz, vti, vt, jj, pj.w, idi, step);
+      fx = fmaf(t.x, t.y, fx);
+      fy = fmaf(t.x, t.z, fy);
+      fz = fmaf(t.x, t.w, fz);
     }
     if (cnt < kListCap) break;  // the cells ran out before the list filled
     cnt = 0;
   }
 
-  const float4 f_old = A.frc[i];
-  A.frc[i] = make_float4(fx, fy, fz, 0.0f);
-  if (kick && vti.w == 0.0f) {
-    // Closing half-kick: v(t+dt) = v(t) + dt/2 (F(t) + F(t+dt)), F = f + g.
-    float4 v = A.vel[i];
-    v.x = fmaf(P.half_dt, (f_old.x + fx) + 2.0f * P.g[0], v.x);
-    v.y = fmaf(P.half_dt, (f_old.y + fy) + 2.0f * P.g[1], v.y);
-    v.z = fmaf(P.half_dt, (f_old.z + fz) + 2.0f * P.g[2], v.z);
-    A.vel[i] = v;
-  }
-  if (!(isfinite(fx) && isfinite(fy) && isfinite(fz)))
-    atomicOr(&ctr->status, ST_NAN);
+  finish_target(P, A, i, vti, fx, fy, fz, ctr, kick);
 }
 
 // A single system takes its parameters by value (they stay in the kernel-parameter
