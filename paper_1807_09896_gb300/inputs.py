@@ -15,6 +15,11 @@ Workloads (DPD units, r_c = 1, rho = 3):
   layers meet through the periodic wrap, so the fluid sees walls only.
   Fluid particles are uniform in the gap, solid particles uniform in the
   layers (the paper's frozen boundary particles, Sec. II.C).
+* ``channel_2d(Lx, W)`` -- the planar (2-D) channel of Sec. III.A, run as a
+  single layer of particles: box Lx x (W + 2 layer) x 3 with every particle at
+  z = 1.5 and zero z velocity, walls at y = 0 and y = W.  Pair forces lie along
+  the separation, which has no z component, so the layer stays exactly planar
+  and the system is a 2-D DPD fluid of areal density rho.
 * ``bulk(L)`` -- a periodic box with no solid (phi = 1 everywhere).
 * ``sphere_pack(L, nspheres, rmin, rmax)`` -- a periodic cube holding
   non-overlapping solid spheres; fluid in the pore space, a 1 r_c solid shell
@@ -225,3 +230,31 @@ def ensemble(nsys: int = 64, seed: int = 0, min_fluid: int = 2000, max_fluid: in
         if min_fluid <= w.n_fluid <= max_fluid:
             out.append(w)
     return out
+
+
+def channel_2d(Lx: float, W: float, rho: float = 4.0, layer: float = 1.0, kBT: float = 1.0,
+               seed: int = 0, h: float = GRID_H) -> Workload:
+    """Planar channel of width W along y between walls at y = 0 and y = W, as one
+    particle layer at z = 1.5 in a box of height 3 (see the module docstring)."""
+    box = (float(Lx), float(W + 2 * layer), 3.0)
+    nx, ny, nz = _grid_dims(box, h)
+    y = np.arange(ny) * h
+    d = np.where(y <= W, np.minimum(y, W - y), -np.minimum(y - W, box[1] - y))
+    phi_y = _phi_from_distance(d)
+    phi = np.broadcast_to(phi_y[None, :, None], (nz, ny, nx)).astype(np.float32).copy()
+    rng = np.random.default_rng(seed)
+    nf = int(round(rho * Lx * W))
+    ns = int(round(rho * Lx * 2 * layer))
+    fy = rng.uniform(0.0, W, size=nf)
+    fy[fy == 0.0] = W / 2
+    fpos = np.stack([rng.uniform(0, Lx, nf), fy, np.full(nf, 1.5)], axis=1)
+    spos = np.stack([rng.uniform(0, Lx, ns), W + rng.uniform(0.0, 2 * layer, ns), np.full(ns, 1.5)],
+                    axis=1)
+    w = _finish(f"channel2d_{Lx:g}x{W:g}", box, phi, h, fpos, spos, kBT, rng, gap=W)
+    w.vel[:, 2] = 0.0
+    fl = w.type == 0
+    if fl.any():
+        w.vel[fl, :2] -= w.vel[fl, :2].mean(axis=0)
+        # Maxwellian in the plane at k_BT: rescale the two in-plane components
+        w.vel[fl, :2] *= np.float32(math.sqrt(kBT) / max(1e-12, float(w.vel[fl, :2].std())))
+    return w
