@@ -20,6 +20,8 @@ Workloads (DPD units, r_c = 1, rho = 3):
   z = 1.5 and zero z velocity, walls at y = 0 and y = W.  Pair forces lie along
   the separation, which has no z component, so the layer stays exactly planar
   and the system is a 2-D DPD fluid of areal density rho.
+* ``cylinder_2d(L, r)`` -- the square array of parallel cylinders of Sec. III.B, as
+  a planar layer like ``channel_2d``: one disk of radius r in a periodic L x L cell.
 * ``bulk(L)`` -- a periodic box with no solid (phi = 1 everywhere).
 * ``sphere_pack(L, nspheres, rmin, rmax)`` -- a periodic cube holding
   non-overlapping solid spheres; fluid in the pore space, a 1 r_c solid shell
@@ -258,3 +260,39 @@ def channel_2d(Lx: float, W: float, rho: float = 4.0, layer: float = 1.0, kBT: f
         # Maxwellian in the plane at k_BT: rescale the two in-plane components
         w.vel[fl, :2] *= np.float32(math.sqrt(kBT) / max(1e-12, float(w.vel[fl, :2].std())))
     return w
+
+
+def cylinder_2d(L: float, r: float, rho: float = 4.0, layer: float = 1.0, kBT: float = 1.0,
+                seed: int = 0, h: float = GRID_H) -> Workload:
+    """One disk of radius r centred in a periodic L x L cell (a square array of
+    parallel cylinders), as a particle layer at z = 1.5 in a box of height 3."""
+    box = (float(L), float(L), 3.0)
+    nx, ny, nz = _grid_dims(box, h)
+    c = np.array([L / 2, L / 2])
+    ax = np.arange(nx) * h
+    xx, yy = np.meshgrid(ax, ax, indexing="xy")
+    dx = xx - c[0]
+    dy = yy - c[1]
+    dx -= L * np.round(dx / L)
+    dy -= L * np.round(dy / L)
+    d2 = np.sqrt(dx * dx + dy * dy) - r
+    phi_xy = _phi_from_distance(d2)  # (ny, nx)
+    phi = np.broadcast_to(phi_xy[None, :, :], (nz, ny, nx)).astype(np.float32).copy()
+    rng = np.random.default_rng(seed)
+    ncand = int(round(rho * L * L))
+    cand = rng.uniform(0, L, size=(ncand, 2))
+    e = cand - c
+    e -= L * np.round(e / L)
+    d = np.sqrt((e * e).sum(1)) - r
+    f2 = cand[d > 0.02]   # see sphere_pack for the empty shell next to curved surfaces
+    s2 = cand[(d <= 0) & (d >= -layer)]
+    fpos = np.stack([f2[:, 0], f2[:, 1], np.full(len(f2), 1.5)], axis=1)
+    spos = np.stack([s2[:, 0], s2[:, 1], np.full(len(s2), 1.5)], axis=1)
+    w = _finish(f"cylinder2d_{L:g}_r{r:g}", box, phi, h, fpos, spos, kBT, rng)
+    w.vel[:, 2] = 0.0
+    fl = w.type == 0
+    if fl.any():
+        w.vel[fl, :2] -= w.vel[fl, :2].mean(axis=0)
+        w.vel[fl, :2] *= np.float32(math.sqrt(kBT) / max(1e-12, float(w.vel[fl, :2].std())))
+    return w
+
