@@ -43,8 +43,11 @@
  *       word, seed high word); u = ((x >> 9) + 0.5) * 2^-23 from output words
  *       0 and 1; xi = sqrt(-2 ln u0) cos(2 pi u1).
  *   R8  pairs at exactly zero separation contribute nothing (no direction).
- *   R9  solid particles are frozen: they get no force, never move, and enter
- *       the dissipative term with velocity v_wall.
+ *   R9  solid particles are frozen: they get no force and enter the dissipative
+ *       term with velocity v_wall.
+ *   R14 a moving wall is a translating solid (Sec. II.C, Couette flow): its
+ *       frozen particles move rigidly with it, r += dt v_wall each step (with
+ *       v_wall = 0 they never move).
  */
 #include <math.h>
 #include <stdint.h>
@@ -402,8 +405,12 @@ int or_step(int n, double* pos, double* vel, double* frc, const int* id, const u
 
   for (int i = 0; i < n; ++i) {
     reflected[i] = 0;
-    if (type[i] != 0) { /* frozen solid (reading R9) */
-      for (int a = 0; a < 3; ++a) { vt[3 * i + a] = vw[a]; Fold[3 * i + a] = 0.0; }
+    if (type[i] != 0) { /* frozen solid (readings R9, R14): moves rigidly at v_wall */
+      for (int a = 0; a < 3; ++a) {
+        vt[3 * i + a] = vw[a];
+        Fold[3 * i + a] = 0.0;
+        if (vw[a] != 0.0) pos[3 * i + a] = wrap_coord(pos[3 * i + a] + dt * vw[a], L[a]);
+      }
       continue;
     }
     double F[3], r0[3], v0[3], r1[3], dr[3];

@@ -21,7 +21,7 @@ namespace dpd {
 // phi < 0 the particle stays at r(t).  The test runs only for particles whose
 // starting cell is flagged in the band mask (Sec. II.C: bulk particles far from
 // phi = 0 need no test); the band is conservative for drifts up to `margin`,
-// which is checked.
+// which is checked.  Frozen (solid) particles translate with the wall velocity.
 // Then the position is wrapped into the box, its cell found, and the particle
 // counted into that cell with one atomic that also gives its arrival slot.
 // ---------------------------------------------------------------------------
@@ -92,6 +92,12 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
     p.z = wrap_coord(z, P.L[2]);
     A.pos[i] = p;
     A.vt[i] = vt;
+  } else if (P.vw[0] != 0.0f || P.vw[1] != 0.0f || P.vw[2] != 0.0f) {
+    // frozen particles are part of the solid, which translates with the wall velocity
+    p.x = wrap_coord(p.x + P.dt * P.vw[0], P.L[0]);
+    p.y = wrap_coord(p.y + P.dt * P.vw[1], P.L[1]);
+    p.z = wrap_coord(p.z + P.dt * P.vw[2], P.L[2]);
+    A.pos[i] = p;
   }
   const uint32_t c = cell_off + (uint32_t)cell_of(P, p.x, p.y, p.z);
   C.key[i] = c;

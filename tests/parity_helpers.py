@@ -118,7 +118,9 @@ def compare_one_step(s, w, p, field, label=""):
     fluid = types == 0
     phi_new = np.ones(len(pos0))
     phi_new[fluid] = oracle.phi_many(field, st0.pos[fluid] + dr[fluid])
-    gpu_refl = fluid & np.all(vel1 == -vel0.astype(np.float32), axis=1) & (np.abs(vel0).sum(1) > 0)
+    # a reflected particle leaves with exactly 2 v_wall - v(t), computed in binary32
+    v_bb = (np.float32(2.0) * np.asarray(p.v_wall, np.float32) - vel0.astype(np.float32))
+    gpu_refl = fluid & np.all(vel1 == v_bb, axis=1) & (np.abs(vel0).sum(1) > 0)
     mismatch = fluid & (gpu_refl != refl)
     assert np.all(np.abs(phi_new[mismatch]) < PHI_AMBIGUOUS), (
         f"{label}: reflection decisions differ away from phi = 0: "
@@ -138,7 +140,11 @@ def compare_one_step(s, w, p, field, label=""):
             f"{label}: {len(bad)} positions differ; worst i={k} gpu={pos1[k]!r} oracle={or1.pos[k]!r} "
             f"start={pos0[k]!r} dr={dr[k]!r} reflected={refl[k]} phi_new={phi_new[k]!r} "
             f"tol={tolp[k]!r}")
-    assert np.all(pos1[~fluid] == pos0[~fluid])
+    if not np.any(p.v_wall):
+        assert np.all(pos1[~fluid] == pos0[~fluid])
+    else:  # the solid translates with the walls
+        ds = min_image(pos1[~fluid].astype(np.float64) - pos0[~fluid] - p.dt * np.asarray(p.v_wall), w.box)
+        assert np.abs(ds).max() < 4 * ulp32(max(w.box))
 
     # forces at t+dt, judged at the GPU's own (binary32) new positions: the oracle's
     # new positions are not rounded to binary32, and the force is steep enough in r

@@ -278,3 +278,15 @@ def test_autotune_keeps_results_and_picks_a_shape():
     b.step(steps_done)
     for x, y in zip(gpu_state(a), gpu_state(b)):
         np.testing.assert_array_equal(x, y)
+
+
+def test_moving_walls_match_the_oracle():
+    """Walls moving at v_wall (Sec. II.C: reflection gives 2 v_wall - v, and frozen
+    particles enter the dissipative force with v_wall)."""
+    w = inputs.channel(6.0, 5.0, 5.0, seed=18)
+    p = params_for(w, seed=12, v_wall=(0.4, -0.2, 0.0))
+    s = make_system(w, p, v_wall_x=0.4, v_wall_y=-0.2)
+    for _ in range(3):
+        compare_one_step(s, w, p, _field(w), label="moving walls")
+        s.step(5)
+    s.close()

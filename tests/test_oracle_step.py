@@ -219,3 +219,20 @@ def test_profile_counts_and_sums_at_bin_centres():
     np.testing.assert_array_equal(out[:, 2], -1.0 * counts)
     np.testing.assert_array_equal(out[:, 3], 2.0 * counts)
     np.testing.assert_array_equal(out[:, 4], 5.25 * counts)
+
+
+def test_moving_wall_translates_the_solid_and_reflects_with_its_velocity():
+    """Sec. II.C: at a wall moving with v_wall the bounce-back velocity is
+    2 v_wall - v(t); the solid itself (its frozen particles) moves at v_wall."""
+    w = inputs.channel(4.0, 3.0, 3.0, seed=2)
+    vw = (0.5, -0.25, 0.0)
+    p = oracle.Params(box=w.box, a_ff=0.0, a_fs=0.0, gamma=0.0, sigma=0.0, dt=0.01, v_wall=vw)
+    pos = np.array([[1.0, 1.0, 0.02], [2.0, 1.5, 4.5]])  # a fluid particle, a solid one
+    vel = np.array([[0.2, 0.1, -3.0], [0.0, 0.0, 0.0]])
+    s = oracle.State(pos, vel, np.zeros((2, 3)), np.array([0, 1], np.int32),
+                     np.array([0, 1], np.uint8))
+    s = oracle.init_forces(s, p)
+    s1, refl = oracle.step(s, p, _field(w), return_reflected=True)
+    assert refl.tolist() == [True, False]
+    np.testing.assert_allclose(s1.vel[0], 2 * np.asarray(vw) - vel[0], atol=1e-15)
+    np.testing.assert_allclose(s1.pos[1], pos[1] + p.dt * np.asarray(vw), atol=1e-15)
