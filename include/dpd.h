@@ -144,6 +144,21 @@ int dpd_get_state(dpd_t* h, float* pos4, float* vel4, float* force4, int* id, ui
 int dpd_velocity_profile(dpd_t* h, int axis, int nbins, double lo, double hi, double* out,
                          int mode);
 
+/* Phase field of an arbitrary geometry (Sec. II.B): relax phi on a periodic grid of
+ * dims[0] x dims[1] x dims[2] nodes (x fastest, host memory, updated in place) of
+ * spacing h by `iters` explicit Euler steps of size dtau in the pseudo time of
+ * Eq. 13, in the scaled coordinates x' = x / eps.  With curvature = 1 the equation is
+ * Eq. 15, d phi/dt' = lap' phi + phi (1 - phi^2) - kappa |grad' phi|, whose curvature
+ * term keeps curved interfaces in place; with 0 it is Eq. 13 in every direction.
+ * Start from a step function (+1 fluid, -1 solid); the steady profile across an
+ * interface is tanh(d / (sqrt(2) eps)) (Eq. 14) and the result can be passed to
+ * dpd_set_phase_field.  dtau must not exceed (h / eps)^2 / 6, every dimension needs
+ * 3 nodes, dims[1] at most 524280 and dims[2] at most 65535 (else DPD_EINVAL).
+ * ms_per_iter (may be NULL) receives the mean device time of one step.  Uses the
+ * current device and the default stream; messages: dpd_last_error(NULL). */
+int dpd_relax_phase_field(float* phi, const int dims[3], double spacing, double eps, int iters,
+                          double dtau, int curvature, double* ms_per_iter);
+
 /* Largest nbins accepted by dpd_velocity_profile_noalloc. */
 #define DPD_NOALLOC_MAX_BINS 4096
 

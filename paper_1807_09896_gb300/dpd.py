@@ -40,6 +40,7 @@ _SIGS = {
     "dpd_adjoint_window": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, _vp, _i, _vp, _vp]),
     "dpd_velocity_profile": (_i, [_vp, _i, _i, _d, _d, _vp, _i]),
     "dpd_velocity_profile_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _vp, _i, _vp]),
+    "dpd_relax_phase_field": (_i, [_vp, _vp, _d, _d, _i, _d, _i, _vp]),
     "dpd_get_stats": (_i, [_vp, _vp]),
     "dpd_set_option": (_i, [_vp, ctypes.c_char_p, _d]),
     "dpd_get_option": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_d)]),
@@ -209,6 +210,21 @@ def dpd_velocity_profile(h, axis: int, nbins: int, lo: float, hi: float, mode: i
         out = np.zeros((nbins, 5), np.float64)
     _check(h, load_library().dpd_velocity_profile(h, axis, nbins, lo, hi, _ptr(out), mode))
     return out
+
+
+def dpd_relax_phase_field(phi, spacing, eps, iters, dtau, curvature=True):
+    """Relax a phase field (float32 array (nz, ny, nx)) by Eq. 15 (curvature=True) or
+    Eq. 13; returns (new array, mean ms per step)."""
+    a = np.ascontiguousarray(phi, np.float32).copy()
+    nz, ny, nx = a.shape
+    dims = np.asarray([nx, ny, nz], np.int32)
+    ms = np.zeros(1, np.float64)
+    rc = load_library().dpd_relax_phase_field(_ptr(a), _ptr(dims), float(spacing), float(eps),
+                                              int(iters), float(dtau), int(bool(curvature)),
+                                              _ptr(ms))
+    if rc != DPD_OK:
+        raise DPDError(rc, dpd_last_error(None))
+    return a, float(ms[0])
 
 
 NOALLOC_MAX_BINS = 4096
