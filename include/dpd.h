@@ -21,8 +21,13 @@
  *      sigma w_R xi_ij / sqrt(dt), xi_ij drawn from Philox4x32-10 keyed by the
  *      pair and the step;
  *   5. the closing half-kick v(t+dt) = v + dt/2 (F(t) + F(t+dt)), skipped
- *      for particles reflected in this step (their velocity is 2 v_wall - v).
- * Solid (frozen) particles never move and get no force (Sec. II.C).
+ *      for particles reflected in this step (their velocity is 2 v_w - v, v_w
+ *      the wall velocity where the particle crossed phi = 0).
+ * Solid (frozen) particles get no force and move with the wall velocity v_w at
+ * their position, which is zero unless the walls move (Sec. II.C moving walls):
+ * v_w(r) = v_wall + d S, d = r[shear_axis] - shear_ref wrapped into
+ * [-L/2, L/2), S = (shear_x, shear_y, shear_z) with no component along the axis
+ * (plane Couette walls slide in their planes; S = 0: all walls move together).
  *
  * Conventions.  DPD units: r_c = 1, particle mass 1.  Arrays of 4 floats per
  * particle ("pos4", "vel4", "force4") hold x, y, z and one unused pad float.
@@ -78,7 +83,7 @@ enum { DPD_HOST = 0, DPD_DEVICE = 1 };
  * dt          time step.
  * body_force  acceleration g added to the force on every fluid particle.
  * Options (dpd_set_option) start at: lambda 0.65, band_margin 0.5,
- * reflect_variant 0, seed 0, system 0, v_wall 0, sample_every 0. */
+ * reflect_variant 0, seed 0, system 0, v_wall 0, shear 0, sample_every 0. */
 int dpd_create(dpd_t** h, const double box[3], double rho, const double a_ij[4], double gamma,
                double sigma, double kBT, double dt, const double body_force[3]);
 
@@ -92,7 +97,7 @@ int dpd_set_phase_field(dpd_t* h, const float* grid, const int dims[3], double s
 /* Load n particles (any order): pos4 positions (wrapped into the box), vel4
  * velocities, id a permutation of 0..n-1, type 0 fluid / 1 solid.  Computes the
  * pair force f(0) at the given state (predicted velocity = v).  Solid
- * velocities are ignored (frozen at v_wall).  Fails with DPD_ELOST if a fluid
+ * velocities are ignored (they move with the wall velocity).  Fails with DPD_ELOST if a fluid
  * particle sits at phi < 0.  The step counter is kept (see option "step"). */
 int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, const int* id,
                       const uint8_t* type, int where);
@@ -128,7 +133,9 @@ int dpd_time_phases(dpd_t* h, int nsteps, double* ms);
 int dpd_autotune(dpd_t* h, int nsteps, double* ms_per_variant, int* chosen);
 
 /* Copy the state in id order: pos4 / vel4 / force4 (n x 4 floats; the force is
- * the pair force f without the body force; solid particles have f = 0), id
+ * the pair force f without the body force; solid particles have f = 0 and the
+ * velocity 0; vel4[4 i + 3] is 1 if particle i was reflected in the last step,
+ * else 0), id
  * (n ints, equal to 0..n-1) and type (n bytes).  Any output pointer may be
  * NULL.  Synchronises the handle's stream. */
 int dpd_get_state(dpd_t* h, float* pos4, float* vel4, float* force4, int* id, uint8_t* type,
@@ -198,7 +205,9 @@ int dpd_get_stats(dpd_t* h, double out[8]);
 
 /* Set or read a named option: "lambda", "band_margin", "reflect_variant" (0:
  * displacement of the step, 1: v(t) dt as printed in Eq. 17), "seed" (integer
- * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "sample_every",
+ * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "shear_x|y|z",
+ * "shear_axis" (0-2, default 2), "shear_ref" (the wall velocity field above; a
+ * shear component along shear_axis is DPD_EINVAL), "sample_every",
  * "a_ff", "a_fs", "gamma", "sigma", "g_x", "g_y", "g_z" (the create-time
  * parameters), "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,

@@ -32,6 +32,7 @@ from . import build as _build
 _P_NAMES = [
     "Lx", "Ly", "Lz", "a_ff", "a_fs", "a_sf", "a_ss", "gamma", "sigma", "kBT", "dt",
     "lam", "gx", "gy", "gz", "vwx", "vwy", "vwz", "reflect_variant",
+    "shx", "shy", "shz", "sh_axis", "sh_ref",
 ]
 
 _lib = None
@@ -72,8 +73,10 @@ def lib() -> ctypes.CDLL:
         L.or_phi_many.restype = None
         L.or_step.argtypes = [ctypes.c_int, f64p, f64p, f64p, i32p, u8p, f64p, f32p, i32p,
                               ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
-                              ctypes.c_int, u8p, i64p]
+                              ctypes.c_int, u8p, i64p, f64p]
         L.or_step.restype = ctypes.c_int
+        L.or_wall_velocities.argtypes = [ctypes.c_int, f64p, u8p, f64p, f64p]
+        L.or_wall_velocities.restype = None
         L.or_profile.argtypes = [ctypes.c_int, f32p, f64p, u8p, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, ctypes.c_double, f64p]
         L.or_profile.restype = None
@@ -100,10 +103,14 @@ class Params:
     reflect_variant: int = 0
     seed: int = 0
     sys: int = 0
+    shear: tuple = (0.0, 0.0, 0.0)  # d v_wall / d r_axis (plane Couette walls)
+    shear_axis: int = 2
+    shear_ref: float = 0.0
 
     def flat(self) -> np.ndarray:
         v = [*self.box, self.a_ff, self.a_fs, self.a_fs, 0.0, self.gamma, self.sigma, self.kBT,
-             self.dt, self.lam, *self.g, *self.v_wall, float(self.reflect_variant)]
+             self.dt, self.lam, *self.g, *self.v_wall, float(self.reflect_variant),
+             *self.shear, float(self.shear_axis), self.shear_ref]
         assert len(v) == len(_P_NAMES)
         return np.asarray(v, dtype=np.float64)
 
@@ -222,32 +229,51 @@ def init_forces(s: State, p: Params, method: int = 1) -> State:
     """f(0): the pair force at the initial state, with the predicted velocity equal to v(0)."""
     s = s.copy()
     vt = s.vel.copy()
-    vt[s.type != 0] = np.asarray(p.v_wall)
+    solid = s.type != 0
+    vt[solid] = wall_velocities(s.pos, s.type, p)[solid]
     s.frc = forces(s.pos, vt, s.id, s.type, p, s.step, method)
     return s
 
 
-def step(s: State, p: Params, f: Field, method: int = 1, return_reflected: bool = False):
-    """Advance the state by one time step; the new force uses counter step+1."""
+def wall_velocities(pos, types, p: Params) -> np.ndarray:
+    """Wall velocity v_w(r) of every solid particle (zero rows for fluid), reading R18."""
+    pos = _c(np.atleast_2d(pos), np.float64)
+    out = np.zeros((len(pos), 3), np.float64)
+    lib().or_wall_velocities(len(pos), pos.reshape(-1), _c(types, np.uint8), p.flat(), out.reshape(-1))
+    return out
+
+
+def step(s: State, p: Params, f: Field, method: int = 1, return_reflected: bool = False,
+         return_wall_velocity: bool = False):
+    """Advance the state by one time step; the new force uses counter step+1.
+
+    return_reflected adds the per-particle reflection flags; return_wall_velocity
+    adds the wall velocity each particle met this step (solid particles: their own;
+    reflected particles: at the crossing point; others: zero)."""
     s = s.copy()
     n = len(s.pos)
     refl = np.zeros(n, np.uint8)
     stats = np.zeros(2, np.int64)
+    vwall = np.zeros((n, 3), np.float64)
     pos = _c(s.pos, np.float64)
     vel = _c(s.vel, np.float64)
     frc = _c(s.frc, np.float64)
     rc = lib().or_step(n, pos.reshape(-1), vel.reshape(-1), frc.reshape(-1), _c(s.id, np.int32),
                        _c(s.type, np.uint8), p.flat(), _c(f.grid, np.float32).reshape(-1),
-                       f.dims, f.h, s.step + 1, p.sys, p.seed, method, refl, stats)
+                       f.dims, f.h, s.step + 1, p.sys, p.seed, method, refl, stats,
+                       vwall.reshape(-1))
     if rc != 0:
         raise RuntimeError(f"or_step failed ({rc})")
     s.pos, s.vel, s.frc = pos, vel, frc
     s.step += 1
     s.stats = {"reflections": s.stats["reflections"] + int(stats[0]),
                "fallbacks": s.stats["fallbacks"] + int(stats[1])}
+    out = (s,)
     if return_reflected:
-        return s, refl.astype(bool)
-    return s
+        out += (refl.astype(bool),)
+    if return_wall_velocity:
+        out += (vwall,)
+    return out if len(out) > 1 else s
 
 
 def profile(pos_f32, vel, types, axis: int, nbins: int, lo: float, hi: float,

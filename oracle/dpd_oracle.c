@@ -48,6 +48,13 @@
  *   R14 a moving wall is a translating solid (Sec. II.C, Couette flow): its
  *       frozen particles move rigidly with it, r += dt v_wall each step (with
  *       v_wall = 0 they never move).
+ *   R18 walls may move at different velocities (plane Couette flow): the wall
+ *       velocity is the field v_w(r) = v_wall + d S, d the signed distance of
+ *       r from the plane r_axis = ref, wrapped into [-L_axis/2, L_axis/2), and
+ *       S = d v_w / d r_axis with no component along the axis (the walls
+ *       slide in their planes).  A frozen particle moves with v_w at its own
+ *       position; a reflected particle leaves with 2 v_w - v, v_w taken at
+ *       the crossing point r + (1 - s) dr of Eq. 17.  S = 0 gives R14.
  */
 #include <math.h>
 #include <stdint.h>
@@ -69,6 +76,8 @@ enum {
   P_GX, P_GY, P_GZ,          /* body force on fluid particles (Sec. III.A) */
   P_VWX, P_VWY, P_VWZ,       /* wall velocity (Sec. II.C) */
   P_REFLECT_VARIANT,
+  P_SHX, P_SHY, P_SHZ,       /* wall shear: d v_wall / d r_axis (reading R18) */
+  P_SHAXIS, P_SHREF,         /* its gradient axis and the plane where v_w = v_wall */
   P_COUNT
 };
 
@@ -285,6 +294,17 @@ long or_pairs(int n, const double* pos, const double* L, int method, long cap, i
 /*   f_ij = [ a_ij w_C - gamma w_D (rhat . v_ij) + sigma w_R xi/sqrt(dt) ] rhat */
 /*   w_C = w_R = 1 - r, w_D = (1 - r)^2 for r < 1.                     */
 /* ------------------------------------------------------------------ */
+/* Wall velocity at a point whose coordinate along the shear axis is xa (R18). */
+static void wall_velocity(const double* P, double xa, double out[3]) {
+  const int ax = (int)P[P_SHAXIS];
+  const double L = P[P_LX + ax];
+  double d = xa - P[P_SHREF];
+  d -= L * floor(d / L + 0.5); /* nearest image: d in [-L/2, L/2) */
+  out[0] = P[P_VWX] + d * P[P_SHX];
+  out[1] = P[P_VWY] + d * P[P_SHY];
+  out[2] = P[P_VWZ] + d * P[P_SHZ];
+}
+
 static void pair_force(const double* P, const double d[3], double r, const double vij[3],
                        int ti, int tj, double xi, double f[3]) {
   double a = P[P_AFF + 2 * ti + tj];
@@ -346,7 +366,7 @@ int or_forces_sel(int n, const double* pos, const double* vt, const int* id,
         if (type[j] == 0) {
           vj[0] = vt[3 * j]; vj[1] = vt[3 * j + 1]; vj[2] = vt[3 * j + 2];
         } else {
-          vj[0] = P[P_VWX]; vj[1] = P[P_VWY]; vj[2] = P[P_VWZ];
+          wall_velocity(P, pos[3 * j + (int)P[P_SHAXIS]], vj); /* R9, R18 */
         }
         double vij[3] = {vt[3 * i] - vj[0], vt[3 * i + 1] - vj[1], vt[3 * i + 2] - vj[2]};
         double xi = or_xi((uint32_t)id[i], (uint32_t)id[j], step, sys, seed);
@@ -391,13 +411,27 @@ static double wrap_coord(double x, double L) {
   return w;
 }
 
+/* Wall velocity of every solid particle at its position (zero for fluid). */
+void or_wall_velocities(int n, const double* pos, const uint8_t* type, const double* P,
+                        double* out) {
+  const int ax = (int)P[P_SHAXIS];
+  for (int i = 0; i < n; ++i) {
+    if (type[i] != 0) {
+      wall_velocity(P, pos[3 * i + ax], out + 3 * i);
+    } else {
+      out[3 * i] = out[3 * i + 1] = out[3 * i + 2] = 0.0;
+    }
+  }
+}
+
 int or_step(int n, double* pos, double* vel, double* frc, const int* id, const uint8_t* type,
             const double* P, const float* grid, const int* dims, double h, uint32_t step_next,
-            uint32_t sys, uint64_t seed, int method, uint8_t* reflected, long* stats) {
+            uint32_t sys, uint64_t seed, int method, uint8_t* reflected, long* stats,
+            double* vwall) {
   const double dt = P[P_DT], lam = P[P_LAMBDA];
   const double L[3] = {P[P_LX], P[P_LY], P[P_LZ]};
   const double g[3] = {P[P_GX], P[P_GY], P[P_GZ]};
-  const double vw[3] = {P[P_VWX], P[P_VWY], P[P_VWZ]};
+  const int ax = (int)P[P_SHAXIS];
   double* vt = (double*)calloc((size_t)3 * (n > 0 ? n : 1), sizeof(double));
   double* Fold = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
   if (!vt || !Fold) { free(vt); free(Fold); return -2; }
@@ -405,14 +439,18 @@ int or_step(int n, double* pos, double* vel, double* frc, const int* id, const u
 
   for (int i = 0; i < n; ++i) {
     reflected[i] = 0;
-    if (type[i] != 0) { /* frozen solid (readings R9, R14): moves rigidly at v_wall */
+    if (type[i] != 0) { /* frozen solid (readings R9, R14, R18): moves with the wall */
+      double vw[3];
+      wall_velocity(P, pos[3 * i + ax], vw);
       for (int a = 0; a < 3; ++a) {
         vt[3 * i + a] = vw[a];
         Fold[3 * i + a] = 0.0;
         if (vw[a] != 0.0) pos[3 * i + a] = wrap_coord(pos[3 * i + a] + dt * vw[a], L[a]);
+        if (vwall) vwall[3 * i + a] = vw[a];
       }
       continue;
     }
+    if (vwall) vwall[3 * i] = vwall[3 * i + 1] = vwall[3 * i + 2] = 0.0;
     double F[3], r0[3], v0[3], r1[3], dr[3];
     for (int a = 0; a < 3; ++a) {
       F[a] = frc[3 * i + a] + g[a];
@@ -430,6 +468,8 @@ int or_step(int n, double* pos, double* vel, double* frc, const int* id, const u
       double A = atanh(-clamp_phi(phi_new)); /* CD of Fig. 4 over sqrt(2) eps */
       double B = atanh(clamp_phi(phi_old));  /* AC of Fig. 4 over sqrt(2) eps */
       double s = A / (A + B);
+      double vw[3]; /* wall velocity at the crossing point r + (1 - s) dr (R18) */
+      wall_velocity(P, r0[ax] + (1.0 - s) * dr[ax], vw);
       double disp[3];
       for (int a = 0; a < 3; ++a)
         disp[a] = (P[P_REFLECT_VARIANT] == 1.0) ? (v0[a] - vw[a]) * dt : dr[a];
@@ -445,6 +485,7 @@ int or_step(int n, double* pos, double* vel, double* frc, const int* id, const u
         double vb = 2.0 * vw[a] - v0[a];
         vel[3 * i + a] = vb;
         vt[3 * i + a] = vb;
+        if (vwall) vwall[3 * i + a] = vw[a];
       }
       reflected[i] = 1;
       ++nrefl;

@@ -36,8 +36,12 @@ StepParams make_params(const dpd_system* h) {
     P.inv_edge[a] = (float)(h->nc[a] / h->box[a]);
     P.g[a] = (float)h->g[a];
     P.vw[a] = (float)h->vw[a];
+    P.sh[a] = (float)h->shear[a];
+    if (h->vw[a] != 0.0 || h->shear[a] != 0.0) P.moving = 1;
     P.pd[a] = h->pd[a];
   }
+  P.sh_axis = h->shear_axis;
+  P.sh_ref = (float)h->shear_ref;
   P.ncells = h->ncells;
   P.dt = (float)h->dt;
   P.half_dt = (float)(0.5 * h->dt);
@@ -467,6 +471,18 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     h->sys = (uint32_t)v;
   } else if (k == "v_wall_x" || k == "v_wall_y" || k == "v_wall_z") {
     h->vw[k.back() - 'x'] = v;
+  } else if (k == "shear_x" || k == "shear_y" || k == "shear_z") {
+    const int c = k.back() - 'x';
+    if (c == h->shear_axis && v != 0.0)
+      return fail(h, DPD_EINVAL, "shear along its own axis would move the walls through the phase field");
+    h->shear[c] = v;
+  } else if (k == "shear_axis") {
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, DPD_EINVAL, "shear_axis must be 0, 1 or 2");
+    if (h->shear[(int)v] != 0.0)
+      return fail(h, DPD_EINVAL, "shear along its own axis would move the walls through the phase field");
+    h->shear_axis = (int)v;
+  } else if (k == "shear_ref") {
+    h->shear_ref = v;
   } else if (k == "sample_every") {
     if (v < 0 || v != std::floor(v)) return fail(h, DPD_EINVAL, "sample_every must be a whole number");
     h->sample_every = (int)v;
@@ -510,6 +526,9 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "seed") *v = (double)h->seed;
   else if (k == "system") *v = h->sys;
   else if (k == "v_wall_x" || k == "v_wall_y" || k == "v_wall_z") *v = h->vw[k.back() - 'x'];
+  else if (k == "shear_x" || k == "shear_y" || k == "shear_z") *v = h->shear[k.back() - 'x'];
+  else if (k == "shear_axis") *v = h->shear_axis;
+  else if (k == "shear_ref") *v = h->shear_ref;
   else if (k == "sample_every") *v = h->sample_every;
   else if (k == "step") *v = (double)h->host_step;
   else if (k == "use_graph") *v = E.use_graph;

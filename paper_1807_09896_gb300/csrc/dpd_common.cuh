@@ -40,6 +40,10 @@ struct StepParams {
   int ncells;
   float dt, half_dt, half_dt2, lam_dt;
   float g[3], vw[3];
+  float sh[3];   // wall velocity field v_w(r) = vw + d sh, d = r[sh_axis] - sh_ref wrapped
+  int sh_axis;   //   into [-L/2, L/2); sh has no component along sh_axis
+  float sh_ref;
+  int moving;    // vw or sh nonzero: the solid moves
   float a_ff, a_fs, gamma, sigma_rsqdt;
   uint32_t seed_lo, seed_hi, sys;
   int reflect_variant;
@@ -49,6 +53,21 @@ struct StepParams {
   float inv_h;
   const uint8_t* band;  // per cell: 1 if a particle starting there may reach phi < 0
 };
+
+// Wall velocity at a point whose coordinate along the shear axis is xa: the field
+// v_w(r) = v_wall + d S of plane Couette walls, d = xa - ref wrapped into
+// [-L/2, L/2) (the walls' own planes, Sec. II.C moving walls).
+__device__ __forceinline__ float3 wall_velocity(const StepParams& P, float xa) {
+  const float L = P.L[P.sh_axis];
+  float d = xa - P.sh_ref;
+  if (d >= 0.5f * L) d -= L;
+  else if (d < -0.5f * L) d += L;
+  return make_float3(fmaf(d, P.sh[0], P.vw[0]), fmaf(d, P.sh[1], P.vw[1]), fmaf(d, P.sh[2], P.vw[2]));
+}
+
+__device__ __forceinline__ float axis_coord(const float4& p, int a) {
+  return a == 0 ? p.x : (a == 1 ? p.y : p.z);
+}
 
 // One system of a batch: its parameters and where its cells and particles sit
 // in the concatenated arrays (a single system is a batch of one).  Systems

@@ -37,16 +37,10 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
   const float r = r2 * inv_r;
   const float w = 1.0f - r;
   const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-  float vjx, vjy, vjz, a;
-  if (is_solid(tagj)) {
-    vjx = P.vw[0]; vjy = P.vw[1]; vjz = P.vw[2];
-    a = P.a_fs;
-  } else {
-    const float4 vtj = __ldg(&vt[jj]);
-    vjx = vtj.x; vjy = vtj.y; vjz = vtj.z;
-    a = P.a_ff;
-  }
-  const float ev = ex * (vti.x - vjx) + ey * (vti.y - vjy) + ez * (vti.z - vjz);
+  // a solid neighbour's vt is the wall velocity at its position
+  const float4 vtj = __ldg(&vt[jj]);
+  const float a = is_solid(tagj) ? P.a_fs : P.a_ff;
+  const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
   const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
   const float mag = w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi);
   return make_float4(mag, ex, ey, ez);

@@ -64,12 +64,17 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
         const float phi_old = fmaxf(phi_at(P, p.x, p.y, p.z), 0.0f);
         const float Ad = atanhf(-clamp_phi(phi_new));
         const float Bd = atanhf(clamp_phi(phi_old));
-        const float s2 = 2.0f * (Ad / (Ad + Bd));
+        const float s = Ad / (Ad + Bd);
+        const float s2 = 2.0f * s;
+        // wall velocity at the crossing point r + (1 - s) dr
+        const int ax = P.sh_axis;
+        const float dra = ax == 0 ? dx : (ax == 1 ? dy : dz);
+        const float3 vw = wall_velocity(P, fmaf(1.0f - s, dra, axis_coord(p, ax)));
         float ex = dx, ey = dy, ez = dz;
         if (P.reflect_variant == 1) {
-          ex = (v.x - P.vw[0]) * P.dt;
-          ey = (v.y - P.vw[1]) * P.dt;
-          ez = (v.z - P.vw[2]) * P.dt;
+          ex = (v.x - vw.x) * P.dt;
+          ey = (v.y - vw.y) * P.dt;
+          ez = (v.z - vw.z) * P.dt;
         }
         // r_bb = r' - 2 s e = r + (dr - 2 s e): one rounding, from the exact r
         const float qx = fmaf(-s2, ex, dx), qy = fmaf(-s2, ey, dy), qz = fmaf(-s2, ez, dz);
@@ -80,8 +85,7 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
           atomicAdd(&ctr->fallbacks, 1ull);
         }
         x = bx; y = by; z = bz;
-        const float4 vb = make_float4(2.0f * P.vw[0] - v.x, 2.0f * P.vw[1] - v.y,
-                                      2.0f * P.vw[2] - v.z, 0.0f);
+        const float4 vb = make_float4(2.0f * vw.x - v.x, 2.0f * vw.y - v.y, 2.0f * vw.z - v.z, 0.0f);
         A.vel[i] = vb;
         vt = make_float4(vb.x, vb.y, vb.z, 1.0f);
         atomicAdd(&ctr->reflections, 1ull);
@@ -92,12 +96,16 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
     p.z = wrap_coord(z, P.L[2]);
     A.pos[i] = p;
     A.vt[i] = vt;
-  } else if (P.vw[0] != 0.0f || P.vw[1] != 0.0f || P.vw[2] != 0.0f) {
-    // frozen particles are part of the solid, which translates with the wall velocity
-    p.x = wrap_coord(p.x + P.dt * P.vw[0], P.L[0]);
-    p.y = wrap_coord(p.y + P.dt * P.vw[1], P.L[1]);
-    p.z = wrap_coord(p.z + P.dt * P.vw[2], P.L[2]);
+  } else if (P.moving) {
+    // frozen particles are part of the solid, which moves with the wall velocity at
+    // their position (constant along the motion: the shear has no component along
+    // its axis); it is also their velocity in the dissipative force
+    const float3 vw = wall_velocity(P, axis_coord(p, P.sh_axis));
+    p.x = wrap_coord(p.x + P.dt * vw.x, P.L[0]);
+    p.y = wrap_coord(p.y + P.dt * vw.y, P.L[1]);
+    p.z = wrap_coord(p.z + P.dt * vw.z, P.L[2]);
     A.pos[i] = p;
+    A.vt[i] = make_float4(vw.x, vw.y, vw.z, 0.0f);
   }
   const uint32_t c = cell_off + (uint32_t)cell_of(P, p.x, p.y, p.z);
   C.key[i] = c;
@@ -410,7 +418,10 @@ __global__ void k_load(StepParams P, const float4* in_pos, const float4* in_vel,
   if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) atomicOr(&ctr->status, ST_NAN);
   float4 v = in_vel[i];
   v.w = 0.0f;
-  if (solid) v = make_float4(P.vw[0], P.vw[1], P.vw[2], 0.0f);
+  if (solid) {
+    const float3 vw = wall_velocity(P, axis_coord(p, P.sh_axis));
+    v = make_float4(vw.x, vw.y, vw.z, 0.0f);
+  }
   if (!solid && phi_at(P, p.x, p.y, p.z) < 0.0f) atomicOr(&ctr->status, ST_LOST);
   A.pos[i] = p;
   A.vel[i] = solid ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
@@ -429,7 +440,7 @@ __global__ void k_unsort(Arrays A, int n, float4* out_pos, float4* out_vel, floa
   if (out_pos) out_pos[id] = make_float4(p.x, p.y, p.z, 0.0f);
   if (out_vel) {
     float4 v = A.vel[i];
-    v.w = 0.0f;
+    v.w = A.vt[i].w;  // 1: reflected in the last step
     out_vel[id] = v;
   }
   if (out_frc) {

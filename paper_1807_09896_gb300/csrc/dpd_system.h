@@ -17,6 +17,9 @@ struct dpd_system {
   double lambda = 0.65;
   double g[3] = {0, 0, 0};
   double vw[3] = {0, 0, 0};
+  double shear[3] = {0, 0, 0};  // d v_wall / d r_axis (plane Couette walls)
+  int shear_axis = 2;
+  double shear_ref = 0.0;
   double margin = 0.5;
   uint64_t seed = 0;
   uint32_t sys = 0;

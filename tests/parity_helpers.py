@@ -37,6 +37,12 @@ def make_system(w, p: oracle.Params, load=True, **options):
     s.set_option("seed", p.seed)
     s.set_option("system", p.sys)
     s.set_option("reflect_variant", p.reflect_variant)
+    for c, v in zip("xyz", p.v_wall):
+        s.set_option(f"v_wall_{c}", v)
+    s.set_option("shear_axis", p.shear_axis)
+    s.set_option("shear_ref", p.shear_ref)
+    for c, v in zip("xyz", p.shear):
+        s.set_option(f"shear_{c}", v)
     for k, v in options.items():
         s.set_option(k, v)
     dpd.dpd_set_phase_field(s.h, w.phi, w.h)
@@ -109,8 +115,10 @@ def compare_one_step(s, w, p, field, label=""):
     stats0 = s.stats()
     s.step(1)
     pos1, vel1, frc1, _ = gpu_state(s)
+    gpu_refl = s.state()[1][:, 3] == 1.0  # the library's own flag
     stats1 = s.stats()
-    or1, refl = oracle.step(st0, p, field, return_reflected=True)
+    or1, refl, vwall = oracle.step(st0, p, field, return_reflected=True, return_wall_velocity=True)
+    moving = bool(np.any(p.v_wall) or np.any(p.shear))
 
     # would-be positions and their phase field, to find ambiguous reflection decisions
     F0 = st0.frc + np.asarray(p.g)
@@ -118,10 +126,18 @@ def compare_one_step(s, w, p, field, label=""):
     fluid = types == 0
     phi_new = np.ones(len(pos0))
     phi_new[fluid] = oracle.phi_many(field, st0.pos[fluid] + dr[fluid])
-    # a reflected particle leaves with exactly 2 v_wall - v(t), computed in binary32
-    v_bb = (np.float32(2.0) * np.asarray(p.v_wall, np.float32) - vel0.astype(np.float32))
-    gpu_refl = fluid & np.all(vel1 == v_bb, axis=1) & (np.abs(vel0).sum(1) > 0)
+    assert not np.any(gpu_refl & ~fluid)
     mismatch = fluid & (gpu_refl != refl)
+    both = gpu_refl & refl
+    if not np.any(p.shear):
+        # a reflected particle leaves with exactly 2 v_wall - v(t), computed in binary32
+        v_bb = np.float32(2.0) * np.asarray(p.v_wall, np.float32) - vel0.astype(np.float32)
+        assert np.all(vel1[both] == v_bb[both]), f"{label}: reflected velocities"
+    else:  # the wall velocity at the crossing point, up to binary32 rounding of that point
+        v_bb = 2.0 * vwall - vel0
+        assert np.all(np.abs(vel1[both] - v_bb[both]) <= 1e-5 * (1 + np.abs(v_bb[both]))), \
+            f"{label}: reflected velocities"
+
     assert np.all(np.abs(phi_new[mismatch]) < PHI_AMBIGUOUS), (
         f"{label}: reflection decisions differ away from phi = 0: "
         f"{np.nonzero(mismatch & (np.abs(phi_new) >= PHI_AMBIGUOUS))[0][:10]}")
@@ -140,18 +156,18 @@ def compare_one_step(s, w, p, field, label=""):
             f"{label}: {len(bad)} positions differ; worst i={k} gpu={pos1[k]!r} oracle={or1.pos[k]!r} "
             f"start={pos0[k]!r} dr={dr[k]!r} reflected={refl[k]} phi_new={phi_new[k]!r} "
             f"tol={tolp[k]!r}")
-    if not np.any(p.v_wall):
+    if not moving:
         assert np.all(pos1[~fluid] == pos0[~fluid])
-    else:  # the solid translates with the walls
-        ds = min_image(pos1[~fluid].astype(np.float64) - pos0[~fluid] - p.dt * np.asarray(p.v_wall), w.box)
+    elif (~fluid).any():  # the solid moves with the wall velocity at each frozen particle
+        ds = min_image(pos1[~fluid].astype(np.float64) - pos0[~fluid] - p.dt * vwall[~fluid], w.box)
         assert np.abs(ds).max() < 4 * ulp32(max(w.box))
 
     # forces at t+dt, judged at the GPU's own (binary32) new positions: the oracle's
     # new positions are not rounded to binary32, and the force is steep enough in r
     # that this rounding alone would exceed the force tolerance
     vt = st0.vel + p.lam * p.dt * F0
-    vt[refl] = -st0.vel[refl] + 2 * np.asarray(p.v_wall)
-    vt[~fluid] = np.asarray(p.v_wall)
+    vt[refl] = -st0.vel[refl] + 2 * vwall[refl]
+    vt[~fluid] = vwall[~fluid]
     ids = np.arange(len(pos0))
     f_ref, fabs1 = force_scales(pos1.astype(np.float64), vt, ids, types, p, step0 + 1)
     _, fabs0 = force_scales(st0.pos, st0.vel, ids, types, p, step0)
@@ -163,7 +179,7 @@ def compare_one_step(s, w, p, field, label=""):
 
     # velocities: closing half-kick with the reference force (reversed if reflected)
     v_ref = st0.vel + 0.5 * p.dt * (F0 + f_ref + np.asarray(p.g))
-    v_ref[refl] = -st0.vel[refl] + 2 * np.asarray(p.v_wall)
+    v_ref[refl] = -st0.vel[refl] + 2 * vwall[refl]
     v_ref[~fluid] = 0.0
     dv = np.abs(vel1.astype(np.float64) - v_ref)
     tolv = F_REL * (np.abs(v_ref) + 0.5 * p.dt * (fabs0 + fabs1)[:, None]) + 4 * ulp32(v_ref)

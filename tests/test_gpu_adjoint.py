@@ -200,3 +200,11 @@ def test_adjoint_on_the_32x16x16_channel_over_200_steps_is_stated():
     assert abs(L - L0) <= 1e-3 * abs(L0)
     assert np.all(np.isfinite(g))
     s.close()
+
+
+def test_adjoint_rejects_walls_sliding_at_different_velocities():
+    w, s, loss = _setup(seed=35)
+    s.set_option("shear_x", 0.05)
+    with pytest.raises(dpd.DPDError):
+        adjoint.window_loss_and_grad(s, (25.0, 4.5, 0.05), loss, nsteps=4, ckpt_every=2)
+    s.close()

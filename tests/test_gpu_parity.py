@@ -290,3 +290,28 @@ def test_moving_walls_match_the_oracle():
         compare_one_step(s, w, p, _field(w), label="moving walls")
         s.step(5)
     s.close()
+
+
+def test_couette_walls_match_the_oracle():
+    """Walls sliding at different velocities (wall velocity field v_wall + d S along
+    z, reading R18): reflection with the crossed wall's velocity, frozen particles
+    moving with theirs and entering the dissipative force with it."""
+    w = inputs.channel(6.0, 5.0, 5.0, seed=21)
+    p = params_for(w, seed=14, v_wall=(0.1, 0.0, 0.0), shear=(0.3, -0.12, 0.0), shear_axis=2,
+                   shear_ref=2.5)
+    s = make_system(w, p)
+    for _ in range(3):
+        compare_one_step(s, w, p, _field(w), label="couette walls")
+        s.step(5)
+    s.close()
+
+
+def test_shear_along_its_own_axis_is_rejected():
+    w = inputs.channel(6.0, 5.0, 5.0, seed=21)
+    s = make_system(w, params_for(w), load=False)
+    with pytest.raises(dpd.DPDError):
+        s.set_option("shear_z", 0.1)  # default axis z: would move the walls through phi
+    s.set_option("shear_x", 0.1)
+    with pytest.raises(dpd.DPDError):
+        s.set_option("shear_axis", 0)
+    s.close()

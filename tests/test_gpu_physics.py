@@ -131,3 +131,36 @@ def test_fluid_between_walls_moving_together_takes_their_velocity():
     print(f"moving walls at 0.3: fluid moves at {v:.4f}")
     assert abs(v - 0.3) < 0.015
     s.close()
+
+
+def test_couette_flow_between_walls_sliding_oppositely_is_linear():
+    """Walls at z = 0 and z = H sliding at -U and +U (Sec. II.C moving walls): the
+    steady profile is u(z) = U (2z/H - 1), linear through zero at mid-gap, reaching
+    the wall velocities at the phi = 0 surfaces (no slip)."""
+    H, U = 10.0, 0.5
+    w = inputs.channel(20.0, 20.0, H, seed=23)
+    z = w.pos[:, 2].astype(np.float64)
+    fluid = w.type == 0
+    w.vel[fluid, 0] += (U * (2 * z / H - 1))[fluid].astype(np.float32)  # start near the profile
+    p = params_for(w, seed=6, shear=(2 * U / H, 0.0, 0.0), shear_axis=2, shear_ref=H / 2)
+    s = make_system(w, p)
+    s.step(10000)
+    nb = 40
+    s.profile(2, nb, 0.0, H, mode=3)
+    s.set_option("sample_every", 5)
+    s.step(20000)
+    prof = s.profile(2, nb, 0.0, H, mode=2)
+    u = prof[:, 1] / prof[:, 0]
+    zc = (np.arange(nb) + 0.5) * H / nb
+    inner = (zc > 1.0) & (zc < H - 1.0)
+    c2, c1, c0 = np.polyfit(zc[inner] - H / 2, u[inner], 2)
+    slope = c1 / (2 * U / H)
+    u_lo, u_hi = c0 - c1 * H / 2, c0 + c1 * H / 2  # the linear part extrapolated to the walls
+    print(f"Couette: slope {slope:.4f} of 2U/H, mid-gap {c0:.4f}, curvature {c2:.2e}, "
+          f"u(0) {u_lo:.4f} u(H) {u_hi:.4f} (walls -{U} / +{U}), "
+          f"reflections {s.stats()[5]:.0f}, fallbacks {s.stats()[6]:.0f}")
+    assert 0.9 < slope < 1.05
+    assert abs(c0) < 0.02
+    assert abs(c2) * (H / 2) ** 2 < 0.03
+    assert abs(u_lo + U) < 0.05 and abs(u_hi - U) < 0.05
+    s.close()

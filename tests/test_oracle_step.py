@@ -236,3 +236,55 @@ def test_moving_wall_translates_the_solid_and_reflects_with_its_velocity():
     assert refl.tolist() == [True, False]
     np.testing.assert_allclose(s1.vel[0], 2 * np.asarray(vw) - vel[0], atol=1e-15)
     np.testing.assert_allclose(s1.pos[1], pos[1] + p.dt * np.asarray(vw), atol=1e-15)
+
+
+def test_couette_walls_slide_oppositely_and_reflect_with_their_own_velocity():
+    """Plane Couette walls (Sec. II.C moving walls, reading R18): the wall at z = H
+    slides at +U and the one at z = 0 at -U, from the field v_w = (z - H/2) 2U/H.
+    Frozen particles at either surface move with their wall; a particle bouncing off
+    a wall leaves with 2 v_w - v of that wall (crossing point within ~0.01 of it)."""
+    H, U = 3.0, 0.6
+    w = inputs.channel(4.0, 3.0, H, seed=2)  # box z: fluid (0, H), solids up to H + 1, wrap at H + 2
+    p = oracle.Params(box=w.box, a_ff=0.0, a_fs=0.0, gamma=0.0, sigma=0.0, dt=0.01,
+                      shear=(2 * U / H, 0.0, 0.0), shear_axis=2, shear_ref=H / 2)
+    pos = np.array([[1.0, 1.0, 0.02], [2.0, 1.0, H - 0.02],   # fluid heading into each wall
+                    [1.5, 1.5, H], [2.5, 1.5, 0.0], [0.5, 0.5, H + 1.5]])  # solids
+    vel = np.array([[0.2, 0.1, -3.0], [0.2, 0.1, 3.0], [0, 0, 0], [0, 0, 0], [0, 0, 0]], float)
+    types = np.array([0, 0, 1, 1, 1], np.uint8)
+    s = oracle.State(pos, vel, np.zeros((5, 3)), np.arange(5, dtype=np.int32), types)
+    s = oracle.init_forces(s, p)
+    s1, refl, vw = oracle.step(s, p, _field(w), return_reflected=True, return_wall_velocity=True)
+    assert refl.tolist() == [True, True, False, False, False]
+    np.testing.assert_allclose(s1.vel[0], [-2 * U - 0.2, -0.1, 3.0], atol=0.01)  # lower wall: -U
+    np.testing.assert_allclose(s1.vel[1], [2 * U - 0.2, -0.1, -3.0], atol=0.01)  # upper wall: +U
+    np.testing.assert_allclose(s1.vel[:2], 2 * vw[:2] - vel[:2], atol=1e-15)
+    # solids: the upper surface moves at +U, the lower at -U, the layer between them
+    # (z = H + 1.5, i.e. 0.5 below the lower surface through the wrap) at -U (1 + 1/H)
+    np.testing.assert_allclose(vw[2:, 0], [U, -U, -U * (1 + 1.0 / H)], atol=1e-12)
+    np.testing.assert_allclose(s1.pos[2:, 0], pos[2:, 0] + p.dt * vw[2:, 0], atol=1e-15)
+    np.testing.assert_array_equal(s1.pos[2:, 1:], pos[2:, 1:])
+
+
+def test_couette_walls_drag_nearby_fluid_along_their_own_velocity():
+    """Frozen particles enter the dissipative force (Eq. 6) with the velocity of their
+    own wall (reading R18): a fluid particle at rest near the upper wall (+U) is
+    dragged towards +x, its mirror image near the lower wall (-U) equally towards -x,
+    and with resting walls neither feels anything."""
+    H, U = 3.0, 0.6
+    w = inputs.channel(4.0, 3.0, H, seed=2)
+    pos = np.array([[1.0, 1.0, H - 0.3], [1.3, 1.0, H + 0.3],       # near the upper wall
+                    [1.0, 2.0, 0.3], [1.3, 2.0, H + 2 - 0.3]])      # mirror, through the wrap
+    types = np.array([0, 1, 0, 1], np.uint8)
+    ids = np.arange(4, dtype=np.int32)
+    out = []
+    for shear in ((2 * U / H, 0.0, 0.0), (0.0, 0.0, 0.0)):
+        p = oracle.Params(box=w.box, a_ff=0.0, a_fs=0.0, gamma=4.5, sigma=0.0, dt=0.01,
+                          shear=shear, shear_axis=2, shear_ref=H / 2)
+        out.append(oracle.forces(pos, np.zeros((4, 3)), ids, types, p, 0))
+    f, f0 = out
+    assert f[0, 0] > 0 and f[2, 0] < 0
+    np.testing.assert_allclose(f[2, 0], -f[0, 0], rtol=1e-12)
+    # mirroring z flips f_z and reversing the wall velocity flips the dissipative
+    # force: together f_z is unchanged
+    np.testing.assert_allclose(f[2, 2], f[0, 2], rtol=1e-12)
+    np.testing.assert_array_equal(f0, 0.0)
