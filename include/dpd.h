@@ -207,7 +207,14 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * displacement of the step, 1: v(t) dt as printed in Eq. 17), "seed" (integer
  * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "shear_x|y|z",
  * "shear_axis" (0-2, default 2), "shear_ref" (the wall velocity field above; a
- * shear component along shear_axis is DPD_EINVAL), "sample_every",
+ * shear component along shear_axis is DPD_EINVAL), "force_law" (0: the soft
+ * repulsion a_ij w of Eq. 4; 1: the attractive/repulsive pair energy of Eq. 22,
+ * E = S^r W(r, r0^r) - S^a W(r, r0^a) with the cubic spline W of Eq. 23, whose
+ * conservative force is -dE/dr along r_ij (Eq. 24); the dissipative and random
+ * forces are unchanged), its parameters "S_r_ff", "S_a_ff", "S_r_fs", "S_a_fs"
+ * (fluid-fluid and fluid-solid strengths; defaults 37.5, 18.75, 75, 37.5 as in
+ * the paper's wetting example), "r0_r", "r0_a" (ranges in (0, 1]; defaults 0.73,
+ * 1), "sph_dim" (D of Eq. 23's normalisation, 1-3; default 3), "sample_every",
  * "a_ff", "a_fs", "gamma", "sigma", "g_x", "g_y", "g_z" (the create-time
  * parameters), "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
@@ -242,7 +249,8 @@ int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
  * dL/da_fs, dL/dgamma, dL/dg_x; loss_out (may be NULL) receives L.
  * Memory: a checkpoint every ckpt_every steps (nsteps must be a multiple) and a
  * record of ckpt_every steps; the backward pass recomputes one segment at a
- * time.  Requires reflect_variant 0. */
+ * time.  Requires reflect_variant 0, force_law 0 and walls moving together
+ * (shear 0); otherwise DPD_EINVAL. */
 int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
                        double wall_hi, int nbins, double bin_width, const double* target,
                        int tie_sigma, double* loss_out, double grad[3]);
@@ -256,8 +264,9 @@ int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wa
  * counter: a system advanced in a batch follows bit for bit the trajectory it
  * follows alone.  The member handles are not advanced (their state stays as it
  * was at dpd_batch_create); the batch reads their phase fields and band masks,
- * so they must outlive the batch and keep their phase field.  Error messages of
- * dpd_batch_create: dpd_batch_last_error(NULL). */
+ * so they must outlive the batch and keep their phase field.  All members must
+ * use the same force_law (DPD_EINVAL).  Error messages of dpd_batch_create:
+ * dpd_batch_last_error(NULL). */
 typedef struct dpd_batch dpd_batch_t;
 
 int dpd_batch_create(dpd_batch_t** hb, int nsys, dpd_t* const* systems);

@@ -33,6 +33,7 @@ _P_NAMES = [
     "Lx", "Ly", "Lz", "a_ff", "a_fs", "a_sf", "a_ss", "gamma", "sigma", "kBT", "dt",
     "lam", "gx", "gy", "gz", "vwx", "vwy", "vwz", "reflect_variant",
     "shx", "shy", "shz", "sh_axis", "sh_ref",
+    "force_law", "S_r_ff", "S_a_ff", "S_r_fs", "S_a_fs", "r0_r", "r0_a", "sph_dim",
 ]
 
 _lib = None
@@ -77,6 +78,11 @@ def lib() -> ctypes.CDLL:
         L.or_step.restype = ctypes.c_int
         L.or_wall_velocities.argtypes = [ctypes.c_int, f64p, u8p, f64p, f64p]
         L.or_wall_velocities.restype = None
+        for fn in ("or_sph_W", "or_sph_dWdr"):
+            getattr(L, fn).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+            getattr(L, fn).restype = ctypes.c_double
+        L.or_sph_energy.argtypes = [f64p, ctypes.c_double, ctypes.c_int]
+        L.or_sph_energy.restype = ctypes.c_double
         L.or_profile.argtypes = [ctypes.c_int, f32p, f64p, u8p, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, ctypes.c_double, f64p]
         L.or_profile.restype = None
@@ -106,11 +112,22 @@ class Params:
     shear: tuple = (0.0, 0.0, 0.0)  # d v_wall / d r_axis (plane Couette walls)
     shear_axis: int = 2
     shear_ref: float = 0.0
+    # attractive/repulsive SPH-kernel force (Eqs. 22-24), the paper's wetting values
+    force_law: int = 0
+    S_r_ff: float = 37.5
+    S_a_ff: float = 18.75
+    S_r_fs: float = 75.0
+    S_a_fs: float = 37.5
+    r0_r: float = 0.73
+    r0_a: float = 1.0
+    sph_dim: int = 3
 
     def flat(self) -> np.ndarray:
         v = [*self.box, self.a_ff, self.a_fs, self.a_fs, 0.0, self.gamma, self.sigma, self.kBT,
              self.dt, self.lam, *self.g, *self.v_wall, float(self.reflect_variant),
-             *self.shear, float(self.shear_axis), self.shear_ref]
+             *self.shear, float(self.shear_axis), self.shear_ref,
+             float(self.force_law), self.S_r_ff, self.S_a_ff, self.S_r_fs, self.S_a_fs,
+             self.r0_r, self.r0_a, float(self.sph_dim)]
         assert len(v) == len(_P_NAMES)
         return np.asarray(v, dtype=np.float64)
 
@@ -233,6 +250,21 @@ def init_forces(s: State, p: Params, method: int = 1) -> State:
     vt[solid] = wall_velocities(s.pos, s.type, p)[solid]
     s.frc = forces(s.pos, vt, s.id, s.type, p, s.step, method)
     return s
+
+
+def sph_W(r: float, r0: float, D: int) -> float:
+    """Smoothing function of Eq. 23 with support scale r0 in D dimensions."""
+    return lib().or_sph_W(float(r), float(r0), int(D))
+
+
+def sph_dWdr(r: float, r0: float, D: int) -> float:
+    """dW/dr of Eq. 23."""
+    return lib().or_sph_dWdr(float(r), float(r0), int(D))
+
+
+def sph_energy(p: Params, r: float, fluid_solid: bool = False) -> float:
+    """Pair energy of Eq. 22 with the strengths of p."""
+    return lib().or_sph_energy(p.flat(), float(r), int(bool(fluid_solid)))
 
 
 def wall_velocities(pos, types, p: Params) -> np.ndarray:

@@ -55,6 +55,13 @@
  *       slide in their planes).  A frozen particle moves with v_w at its own
  *       position; a reflected particle leaves with 2 v_w - v, v_w taken at
  *       the crossing point r + (1 - s) dr of Eq. 17.  S = 0 gives R14.
+ *   R19 Eq. 24 as printed adds +W' rhat; W' < 0, so the term named repulsive
+ *       would attract.  The force is read as minus the derivative of the
+ *       energy of Eq. 22, f_i = -sum_j [S^r W'(r^r) - S^a W'(r^a)] rhat_ij,
+ *       rhat_ij pointing from j to i.  Fluid-solid pairs use their own
+ *       strengths (the paper doubles the fluid-fluid ones); the dissipative
+ *       and random parts keep the weights of Eqs. 5-8 with r_c = 1, so both
+ *       ranges must be <= 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +85,11 @@ enum {
   P_REFLECT_VARIANT,
   P_SHX, P_SHY, P_SHZ,       /* wall shear: d v_wall / d r_axis (reading R18) */
   P_SHAXIS, P_SHREF,         /* its gradient axis and the plane where v_w = v_wall */
+  P_FORCE_LAW,               /* 0: Eq. 4 soft repulsion; 1: Eqs. 22-24 */
+  P_SR_FF, P_SA_FF,          /* S^r, S^a fluid-fluid (Eq. 22) */
+  P_SR_FS, P_SA_FS,          /* S^r, S^a fluid-solid */
+  P_R0R, P_R0A,              /* r0^r, r0^a */
+  P_SPH_DIM,                 /* D of Eq. 23 */
   P_COUNT
 };
 
@@ -289,11 +301,6 @@ long or_pairs(int n, const double* pos, const double* L, int method, long cap, i
   return m;
 }
 
-/* ------------------------------------------------------------------ */
-/* Pair force, Eqs. 3-10:                                              */
-/*   f_ij = [ a_ij w_C - gamma w_D (rhat . v_ij) + sigma w_R xi/sqrt(dt) ] rhat */
-/*   w_C = w_R = 1 - r, w_D = (1 - r)^2 for r < 1.                     */
-/* ------------------------------------------------------------------ */
 /* Wall velocity at a point whose coordinate along the shear axis is xa (R18). */
 static void wall_velocity(const double* P, double xa, double out[3]) {
   const int ax = (int)P[P_SHAXIS];
@@ -305,15 +312,66 @@ static void wall_velocity(const double* P, double xa, double out[3]) {
   out[2] = P[P_VWZ] + d * P[P_SHZ];
 }
 
+/* ------------------------------------------------------------------ */
+/* Smoothing function of Eq. 23 (the SPH cubic spline) with support     */
+/* scale r0: h = r0 / 2, v = r / h,                                      */
+/*   W = alpha_D / h^D * { 1 - 3/2 v^2 + 3/4 v^3   (0 <= v < 1)          */
+/*                         1/4 (2 - v)^3           (1 <= v < 2)          */
+/*                         0                       (v >= 2) }            */
+/* alpha_D = 2/3, 10/(7 pi), 1/pi for D = 1, 2, 3; and its derivative    */
+/* dW/dr = alpha_D / h^(D+1) * dw/dv.                                    */
+/* ------------------------------------------------------------------ */
+static double sph_alpha(int D) {
+  return D == 1 ? 2.0 / 3.0 : (D == 2 ? 10.0 / (7.0 * M_PI) : 1.0 / M_PI);
+}
+
+double or_sph_W(double r, double r0, int D) {
+  const double h = 0.5 * r0, v = r / h;
+  double w = 0.0;
+  if (v < 1.0) w = 1.0 - 1.5 * v * v + 0.75 * v * v * v;
+  else if (v < 2.0) w = 0.25 * (2.0 - v) * (2.0 - v) * (2.0 - v);
+  return sph_alpha(D) / pow(h, D) * w;
+}
+
+double or_sph_dWdr(double r, double r0, int D) {
+  const double h = 0.5 * r0, v = r / h;
+  double dw = 0.0;
+  if (v < 1.0) dw = -3.0 * v + 2.25 * v * v;
+  else if (v < 2.0) dw = -0.75 * (2.0 - v) * (2.0 - v);
+  return sph_alpha(D) / pow(h, D + 1) * dw;
+}
+
+/* Pair energy of Eq. 22: E = S^r W(r, r0^r) - S^a W(r, r0^a); fs selects the
+ * fluid-solid strengths. */
+double or_sph_energy(const double* P, double r, int fs) {
+  const int D = (int)P[P_SPH_DIM];
+  const double Sr = fs ? P[P_SR_FS] : P[P_SR_FF], Sa = fs ? P[P_SA_FS] : P[P_SA_FF];
+  return Sr * or_sph_W(r, P[P_R0R], D) - Sa * or_sph_W(r, P[P_R0A], D);
+}
+
+/* ------------------------------------------------------------------ */
+/* Pair force, Eqs. 3-10:                                              */
+/*   f_ij = [ C(r) - gamma w_D (rhat . v_ij) + sigma w_R xi/sqrt(dt) ] rhat */
+/*   w_R = 1 - r, w_D = (1 - r)^2 for r < 1, and the conservative part  */
+/*   C(r) = a_ij w_C, w_C = 1 - r (Eq. 4; force law 0) or               */
+/*   C(r) = -dE/dr of Eq. 22 (Eq. 24 read as -dE/dr, reading R19; law 1). */
+/* ------------------------------------------------------------------ */
 static void pair_force(const double* P, const double d[3], double r, const double vij[3],
                        int ti, int tj, double xi, double f[3]) {
-  double a = P[P_AFF + 2 * ti + tj];
   double wC = 1.0 - r;
   double wR = wC;
   double wD = wR * wR;
   double e[3] = {d[0] / r, d[1] / r, d[2] / r};
   double ev = e[0] * vij[0] + e[1] * vij[1] + e[2] * vij[2];
-  double mag = a * wC - P[P_GAMMA] * wD * ev + P[P_SIGMA] * wR * xi / sqrt(P[P_DT]);
+  double cons;
+  if (P[P_FORCE_LAW] == 0.0) {
+    cons = P[P_AFF + 2 * ti + tj] * wC;
+  } else {
+    const int D = (int)P[P_SPH_DIM], fs = ti != tj;
+    const double Sr = fs ? P[P_SR_FS] : P[P_SR_FF], Sa = fs ? P[P_SA_FS] : P[P_SA_FF];
+    cons = -(Sr * or_sph_dWdr(r, P[P_R0R], D) - Sa * or_sph_dWdr(r, P[P_R0A], D));
+  }
+  double mag = cons - P[P_GAMMA] * wD * ev + P[P_SIGMA] * wR * xi / sqrt(P[P_DT]);
   f[0] = mag * e[0];
   f[1] = mag * e[1];
   f[2] = mag * e[2];

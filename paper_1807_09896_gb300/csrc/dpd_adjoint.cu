@@ -360,6 +360,7 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
   if (axis < 0 || axis > 2 || !(wall_hi > wall_lo) || nbins < 1 || nbins > 1024 || !(bin_width > 0))
     return afail(h, DPD_EINVAL, "bad loss layout");
   if (h->reflect_variant != 0) return afail(h, DPD_EINVAL, "the adjoint supports reflect_variant 0");
+  if (h->force_law != 0) return afail(h, DPD_EINVAL, "the adjoint supports force_law 0");
   if (h->shear[0] != 0.0 || h->shear[1] != 0.0 || h->shear[2] != 0.0)
     return afail(h, DPD_EINVAL, "the adjoint supports walls moving together (shear 0)");
   if (tie_sigma && !(h->kBT > 0.0 && h->sigma > 0.0))

@@ -40,6 +40,19 @@ StepParams make_params(const dpd_system* h) {
     if (h->vw[a] != 0.0 || h->shear[a] != 0.0) P.moving = 1;
     P.pd[a] = h->pd[a];
   }
+  P.law = h->force_law;
+  {
+    const int D = h->sph_dim;
+    const double alpha = D == 1 ? 2.0 / 3.0 : (D == 2 ? 10.0 / (7.0 * M_PI) : 1.0 / M_PI);
+    const double hr = 0.5 * h->sph_r0[0], ha = 0.5 * h->sph_r0[1];
+    const double cr = alpha / std::pow(hr, D + 1), ca = alpha / std::pow(ha, D + 1);
+    P.sph_kr_ff = (float)(h->sph_S[0] * cr);
+    P.sph_ka_ff = (float)(h->sph_S[1] * ca);
+    P.sph_kr_fs = (float)(h->sph_S[2] * cr);
+    P.sph_ka_fs = (float)(h->sph_S[3] * ca);
+    P.sph_ihr = (float)(1.0 / hr);
+    P.sph_iha = (float)(1.0 / ha);
+  }
   P.sh_axis = h->shear_axis;
   P.sh_ref = (float)h->shear_ref;
   P.ncells = h->ncells;
@@ -483,6 +496,17 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     h->shear_axis = (int)v;
   } else if (k == "shear_ref") {
     h->shear_ref = v;
+  } else if (k == "force_law") {
+    if (v != 0.0 && v != 1.0) return fail(h, DPD_EINVAL, "force_law must be 0 or 1");
+    h->force_law = (int)v;
+  } else if (k == "S_r_ff" || k == "S_a_ff" || k == "S_r_fs" || k == "S_a_fs") {
+    h->sph_S[(k[5] == 's' ? 2 : 0) + (k[2] == 'a' ? 1 : 0)] = v;
+  } else if (k == "r0_r" || k == "r0_a") {
+    if (!(v > 0.0) || v > 1.0) return fail(h, DPD_EINVAL, "%s must be in (0, 1] (the pair cutoff is 1)", key);
+    h->sph_r0[k[3] == 'a' ? 1 : 0] = v;
+  } else if (k == "sph_dim") {
+    if (v != 1.0 && v != 2.0 && v != 3.0) return fail(h, DPD_EINVAL, "sph_dim must be 1, 2 or 3");
+    h->sph_dim = (int)v;
   } else if (k == "sample_every") {
     if (v < 0 || v != std::floor(v)) return fail(h, DPD_EINVAL, "sample_every must be a whole number");
     h->sample_every = (int)v;
@@ -529,6 +553,11 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "shear_x" || k == "shear_y" || k == "shear_z") *v = h->shear[k.back() - 'x'];
   else if (k == "shear_axis") *v = h->shear_axis;
   else if (k == "shear_ref") *v = h->shear_ref;
+  else if (k == "force_law") *v = h->force_law;
+  else if (k == "S_r_ff" || k == "S_a_ff" || k == "S_r_fs" || k == "S_a_fs")
+    *v = h->sph_S[(k[5] == 's' ? 2 : 0) + (k[2] == 'a' ? 1 : 0)];
+  else if (k == "r0_r" || k == "r0_a") *v = h->sph_r0[k[3] == 'a' ? 1 : 0];
+  else if (k == "sph_dim") *v = h->sph_dim;
   else if (k == "sample_every") *v = h->sample_every;
   else if (k == "step") *v = (double)h->host_step;
   else if (k == "use_graph") *v = E.use_graph;

@@ -77,6 +77,8 @@ int dpd_batch_create(dpd_batch_t** out, int nsys, dpd_t* const* systems) {
     if (!h) return bfail(nullptr, DPD_EINVAL, "system %d is NULL", k);
     if (!h->loaded) return bfail(nullptr, DPD_ESTATE, "system %d has no valid particle state", k);
     if (h->E.h_ctr[0].status) return bfail(nullptr, DPD_ESTATE, "system %d has a pending error", k);
+    if (h->force_law != systems[0]->force_law)
+      return bfail(nullptr, DPD_EINVAL, "system %d uses another force law than system 0", k);
     for (int q = 0; q < k; ++q)
       if (systems[q] == h) return bfail(nullptr, DPD_EINVAL, "system %d appears twice", k);
     n_total += h->E.n;

@@ -52,6 +52,10 @@ struct StepParams {
   int pd[3];
   float inv_h;
   const uint8_t* band;  // per cell: 1 if a particle starting there may reach phi < 0
+  // force law 1 (Eqs. 22-24): C(r) = K_r g(r / h_r) - K_a g(r / h_a), g = -dw/dv of
+  // the cubic spline, K = S alpha_D / h^(D+1); ff and fs strengths
+  int law;
+  float sph_kr_ff, sph_ka_ff, sph_kr_fs, sph_ka_fs, sph_ihr, sph_iha;
 };
 
 // Wall velocity at a point whose coordinate along the shear axis is xa: the field

@@ -25,10 +25,20 @@ namespace dpd {
 // blocks per SM, unroll of the pair loop).  Every shape sums the same pairs in
 // the same order, so all of them give bit-identical forces; dpd_autotune picks
 // the fastest on the device at hand.
+// Slope -dw/dv of the cubic spline of Eq. 23 (w = 1 - 3/2 v^2 + 3/4 v^3 below 1,
+// (2 - v)^3 / 4 below 2, 0 beyond).
+__device__ __forceinline__ float spline_slope(float v) {
+  const float u = 2.0f - v;
+  return v < 1.0f ? v * fmaf(-2.25f, v, 3.0f) : (v < 2.0f ? 0.75f * u * u : 0.0f);
+}
+
 // One pair term of Eq. 2 (Eqs. 3-10) for the separation d = r_i - r_j (|d| < r_c):
 // returns (m, e_x, e_y, e_z) with f_ij = m e, e = d / r, w = 1 - r and
-//   m = w (a_ij - gamma w (e . (vt_i - vt_j)) + sigma xi_ij / sqrt(dt)).
-// Every force kernel evaluates pairs through this function, so they agree bit for bit.
+//   m = C(r) - gamma w^2 (e . (vt_i - vt_j)) + sigma w xi_ij / sqrt(dt),
+// C(r) = a_ij w for force law 0 (Eq. 4) and C(r) = -dE/dr of Eq. 22 for law 1
+// (Eq. 24).  Every force kernel evaluates pairs through this function, so they agree
+// bit for bit.
+template <int kLaw>
 __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float dy, float dz,
                                             float4 vti, const float4* __restrict__ vt, int jj,
                                             float tagj, uint32_t idi, uint32_t step) {
@@ -39,11 +49,20 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
   const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
   // a solid neighbour's vt is the wall velocity at its position
   const float4 vtj = __ldg(&vt[jj]);
-  const float a = is_solid(tagj) ? P.a_fs : P.a_ff;
-  const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
-  const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
-  const float mag = w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi);
-  return make_float4(mag, ex, ey, ez);
+  if constexpr (kLaw == 0) {
+    const float a = is_solid(tagj) ? P.a_fs : P.a_ff;
+    const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
+    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
+    return make_float4(w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi), ex, ey, ez);
+  } else {
+    const bool solid = is_solid(tagj);
+    const float kr = solid ? P.sph_kr_fs : P.sph_kr_ff;
+    const float ka = solid ? P.sph_ka_fs : P.sph_ka_ff;
+    const float c = kr * spline_slope(r * P.sph_ihr) - ka * spline_slope(r * P.sph_iha);
+    const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
+    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
+    return make_float4(fmaf(w, P.sigma_rsqdt * xi - P.gamma * w * ev, c), ex, ey, ez);
+  }
 }
 
 // Store the new pair force of target i and apply the closing half-kick
@@ -63,7 +82,7 @@ __device__ __forceinline__ void finish_target(const StepParams& P, const Arrays&
   if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&ctr->status, ST_NAN);
 }
 
-template <int kForceThreads, int kListCap, int kUnroll>
+template <int kForceThreads, int kListCap, int kUnroll, int kLaw>
 __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* __restrict__ start,
                                            DevCounters* ctr, const Arrays& A, int i, float4 pi,
                                            int (*list)[kForceThreads],
@@ -160,7 +179,7 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
       const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
       const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-      const float4 t = pair_term(P, dx, dy, dz, vti, vt, jj, pj.w, idi, step);
+      const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, idi, step);
       fx = fmaf(t.x, t.y, fx);
       fy = fmaf(t.x, t.z, fy);
       fz = fmaf(t.x, t.w, fz);
@@ -175,7 +194,7 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
 // A single system takes its parameters by value (they stay in the kernel-parameter
 // bank); a batch reads each particle's system from the table.  Both run the same
 // body, so a system computes the same bits alone and in a batch.
-template <int kForceThreads, int kListCap, int kMinBlocks, int kUnroll, bool kBatch>
+template <int kForceThreads, int kListCap, int kMinBlocks, int kUnroll, bool kBatch, int kLaw>
 __global__ void __launch_bounds__(kForceThreads, kMinBlocks)
 k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
         const uint32_t* __restrict__ start_all, int n, DevCounters* ctrs, int kick) {
@@ -187,11 +206,11 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   if (is_solid(pi.w)) return;
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
-    force_body<kForceThreads, kListCap, kUnroll>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk, A,
-                                                 i, pi, list, seg_b, seg_e, kick);
+    force_body<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,
+                                                       A, i, pi, list, seg_b, seg_e, kick);
   } else {
-    force_body<kForceThreads, kListCap, kUnroll>(P0, start_all, ctrs, A, i, pi, list, seg_b, seg_e,
-                                                 kick);
+    force_body<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, ctrs, A, i, pi, list, seg_b,
+                                                       seg_e, kick);
   }
 }
 
@@ -199,12 +218,15 @@ using ForceKernel = void (*)(StepParams, const SysDesc*, int, Arrays, const uint
                              DevCounters*, int);
 
 struct ForceVariant {
-  ForceKernel single, batch;
+  ForceKernel single[2], batch[2];  // by force law
   int threads;
 };
 
-#define DPD_FORCE_VARIANT(T, C, M, U) \
-  { k_force<T, C, M, U, false>, k_force<T, C, M, U, true>, T }
+#define DPD_FORCE_VARIANT(T, C, M, U)                                            \
+  {                                                                              \
+    {k_force<T, C, M, U, false, 0>, k_force<T, C, M, U, false, 1>},              \
+        {k_force<T, C, M, U, true, 0>, k_force<T, C, M, U, true, 1>}, T          \
+  }
 
 static const ForceVariant kForceVariants[] = {
     DPD_FORCE_VARIANT(128, 24, 1, 1), DPD_FORCE_VARIANT(128, 16, 1, 1),
@@ -229,7 +251,9 @@ void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays
   if (variant < 0 || variant >= force_variants()) variant = 0;
   const ForceVariant& fv = kForceVariants[variant];
   const int nb = (n + fv.threads - 1) / fv.threads;
-  (nsys == 1 ? fv.single : fv.batch)<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, n, ctr, kick);
+  const int law = P0.law == 1 ? 1 : 0;  // a batch holds systems of one law
+  (nsys == 1 ? fv.single[law] : fv.batch[law])<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, n, ctr,
+                                                                          kick);
 }
 
 }  // namespace dpd

@@ -20,6 +20,12 @@ struct dpd_system {
   double shear[3] = {0, 0, 0};  // d v_wall / d r_axis (plane Couette walls)
   int shear_axis = 2;
   double shear_ref = 0.0;
+  // conservative force law: 0 soft repulsion (Eq. 4), 1 SPH-kernel attraction and
+  // repulsion (Eqs. 22-24; defaults: the paper's wetting example)
+  int force_law = 0;
+  double sph_S[4] = {37.5, 18.75, 75.0, 37.5};  // S^r_ff, S^a_ff, S^r_fs, S^a_fs
+  double sph_r0[2] = {0.73, 1.0};               // r0^r, r0^a
+  int sph_dim = 3;
   double margin = 0.5;
   uint64_t seed = 0;
   uint32_t sys = 0;

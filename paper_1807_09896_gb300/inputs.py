@@ -135,6 +135,14 @@ def channel(Lx: float, Ly: float, H: float, rho: float = 3.0, layer: float = 1.0
     return _finish(f"channel_{Lx:g}x{Ly:g}x{H:g}", box, phi, h, fpos, spos, kBT, rng, gap=H)
 
 
+def keep(w: Workload, mask) -> Workload:
+    """The particles of w selected by mask, with ids renumbered 0..m-1 in order."""
+    mask = np.asarray(mask, bool)
+    m = int(mask.sum())
+    return Workload(w.name + "_subset", w.box, w.phi, w.h, w.pos[mask].copy(), w.vel[mask].copy(),
+                    np.arange(m, dtype=np.int32), w.type[mask].copy(), w.gap)
+
+
 def bulk(L, rho: float = 3.0, kBT: float = 1.0, seed: int = 0, h: float = GRID_H) -> Workload:
     """Periodic box of fluid with no solid anywhere (phi = 1)."""
     box = tuple(float(x) for x in (L if np.ndim(L) else (L, L, L)))

@@ -43,6 +43,8 @@ def make_system(w, p: oracle.Params, load=True, **options):
     s.set_option("shear_ref", p.shear_ref)
     for c, v in zip("xyz", p.shear):
         s.set_option(f"shear_{c}", v)
+    for k in ("force_law", "S_r_ff", "S_a_ff", "S_r_fs", "S_a_fs", "r0_r", "r0_a", "sph_dim"):
+        s.set_option(k, getattr(p, k))
     for k, v in options.items():
         s.set_option(k, v)
     dpd.dpd_set_phase_field(s.h, w.phi, w.h)

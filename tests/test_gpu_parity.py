@@ -7,6 +7,8 @@ Sizes run from a 3x3x3 box (the smallest cell grid, every cell on the periodic
 seam) through several thread blocks with a ragged tail up to the benchmark's
 channel of about one million fluid particles.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -315,3 +317,28 @@ def test_shear_along_its_own_axis_is_rejected():
     with pytest.raises(dpd.DPDError):
         s.set_option("shear_axis", 0)
     s.close()
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_attractive_repulsive_force_law_matches_the_oracle(dim):
+    """The pair energy of Eq. 22 with the spline of Eq. 23 (force -dE/dr, Eq. 24) and
+    the paper's wetting parameters (kBT 0.5, gamma 4.5, fluid-solid strengths twice
+    the fluid-fluid ones), in a channel: fluid-fluid and fluid-solid pairs, seams."""
+    w = inputs.channel(6.0, 5.0, 5.0, seed=22, kBT=0.5)
+    p = params_for(w, seed=15, force_law=1, sph_dim=dim, kBT=0.5, gamma=4.5,
+                   sigma=math.sqrt(2 * 4.5 * 0.5), g=(0.02, 0.0, 0.0))
+    s = make_system(w, p)
+    for _ in range(3):
+        compare_one_step(s, w, p, _field(w), label=f"force law 1, D={dim}")
+        s.step(5)
+    s.close()
+
+
+def test_batch_rejects_mixed_force_laws():
+    w = inputs.channel(6.0, 5.0, 5.0, seed=22)
+    a = make_system(w, params_for(w))
+    b = make_system(w, params_for(w, force_law=1))
+    with pytest.raises(dpd.DPDError):
+        dpd.Batch([a, b])
+    a.close()
+    b.close()
