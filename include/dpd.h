@@ -123,10 +123,15 @@ enum {
 int dpd_time_phases(dpd_t* h, int nsteps, double* ms);
 
 /* Pick the fastest launch shape of the pair-force kernel for this system on this
- * device.  Every shape (threads per block, pair-list slots per thread, resident
- * blocks, loop unroll) computes bit-identical forces, so the choice affects speed
- * only.  Each shape is timed over nsteps event-timed steps (after one warm-up
- * step); the system advances by (nsteps + 1) x (number of shapes) steps.
+ * device.  There are two algorithms.  Full-shell shapes evaluate every pair from
+ * both sides and sum in binary32 in a fixed order.  Newton's-third-law shapes
+ * (option "force_newton3" = 1) evaluate every pair once, give -f_ij to the partner
+ * and sum in 64-bit fixed point (2^-32 resolution), then a second kernel applies
+ * the closing kick.  Within one algorithm every shape (threads per block, pair-list
+ * slots per thread, resident blocks, loop unroll) computes bit-identical results;
+ * the two algorithms agree to binary32 rounding.  Both are deterministic.  Each
+ * shape is timed over nsteps event-timed steps (after one warm-up step).  The state
+ * and counters are then restored, so tuning does not advance the system.
  * ms_per_variant (may be NULL) receives the mean force time of each shape (size:
  * option "force_variants"); chosen (may be NULL) the index now in use (option
  * "force_variant"). */
@@ -220,7 +225,8 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
  * default 20), "force_variant" (launch shape of the pair-force kernel, see
  * dpd_autotune).  Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
- * enqueued by stepping calls so far), "kernels_per_step", "force_variants". */
+ * enqueued by stepping calls so far), "kernels_per_step", "force_variants",
+ * "force_newton3" (1 if the current shape evaluates each pair once). */
 int dpd_set_option(dpd_t* h, const char* key, double value);
 int dpd_get_option(dpd_t* h, const char* key, double* value);
 

@@ -351,7 +351,6 @@ int dpd_autotune(dpd_t* h, int nsteps, double* ms_per_variant, int* chosen) {
   int rc = sync_params(h);
   if (rc) return rc;
   rc = dpd::engine_autotune(h->E, nsteps, ms_per_variant, chosen);
-  h->host_step += (uint64_t)(nsteps + 1) * dpd::force_variants();
   if (rc) return rc;
   uint32_t st = 0;
   rc = read_status(h, &st);
@@ -564,9 +563,10 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "graph_steps") *v = E.graph_steps;
   else if (k == "ncells") *v = h->ncells;
   else if (k == "kernel_launches") *v = (double)E.launches;
-  else if (k == "kernels_per_step") *v = dpd::kKernelsPerStep;
+  else if (k == "kernels_per_step") *v = dpd::engine_kernels_per_step(E);
   else if (k == "force_variant") *v = E.force_variant;
   else if (k == "force_variants") *v = dpd::force_variants();
+  else if (k == "force_newton3") *v = dpd::force_variant_kernels(E.force_variant) == 2;
   else return fail(h, DPD_EINVAL, "unknown option '%s'", key);
   return DPD_OK;
 }

@@ -265,8 +265,9 @@ int dpd_batch_get_option(dpd_batch_t* b, const char* key, double* v) {
   else if (k == "graph_steps") *v = E.graph_steps;
   else if (k == "force_variant") *v = E.force_variant;
   else if (k == "force_variants") *v = dpd::force_variants();
+  else if (k == "force_newton3") *v = dpd::force_variant_kernels(E.force_variant) == 2;
   else if (k == "kernel_launches") *v = (double)E.launches;
-  else if (k == "kernels_per_step") *v = dpd::kKernelsPerStep;
+  else if (k == "kernels_per_step") *v = dpd::engine_kernels_per_step(E);
   else if (k == "nsys") *v = E.nsys;
   else if (k == "n") *v = E.n;
   else if (k == "ncells") *v = E.ncells;

@@ -51,7 +51,9 @@ static void free_particle_buffers(Engine& E) {
   cudaFree(E.cl.key);
   cudaFree(E.cl.rank);
   cudaFree(E.cl.perm);
+  cudaFree(E.facc);
   E.cl.key = E.cl.rank = E.cl.perm = nullptr;
+  E.facc = nullptr;
   E.cap = 0;
 }
 
@@ -114,6 +116,8 @@ int engine_reserve(Engine& E, int nsys, int n, int ncells) {
     ECU(E, dev_alloc(&E.cl.key, n));
     ECU(E, dev_alloc(&E.cl.rank, n));
     ECU(E, dev_alloc(&E.cl.perm, n));
+    ECU(E, dev_alloc(&E.facc, 3 * (size_t)n));
+    ECU(E, cudaMemsetAsync(E.facc, 0, sizeof(unsigned long long) * 3 * (size_t)n, E.stream));
     E.cap = n;
   }
   E.nsys = nsys;
@@ -138,8 +142,12 @@ void engine_enqueue_sort(Engine& E) {
   E.cur ^= 1;
 }
 
+int engine_kernels_per_step(const Engine& E) {
+  return kKernelsPerStepBase + force_variant_kernels(E.force_variant);
+}
+
 void engine_enqueue_force(Engine& E, int kick) {
-  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, E.arr[E.cur], E.cl.start, E.n, E.d_ctr, kick,
+  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, E.arr[E.cur], E.cl.start, E.facc, E.n, E.d_ctr, kick,
                E.force_variant, E.stream);
 }
 
@@ -151,14 +159,14 @@ static void enqueue_step_from(Engine& E, int c) {
   launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
   launch_scan(E.cl, E.ncells, E.n, E.stream);
   launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
-  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.n, E.d_ctr, 1, E.force_variant,
-               E.stream);
+  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
+               E.force_variant, E.stream);
 }
 
 void engine_enqueue_step(Engine& E) {
   enqueue_step_from(E, E.cur);
   E.cur ^= 1;
-  E.launches += kKernelsPerStep;
+  E.launches += engine_kernels_per_step(E);
 }
 
 static int build_graph(Engine& E, int c) {
@@ -191,7 +199,7 @@ int engine_step(Engine& E, int nsteps) {
       }
       ECU(E, cudaGraphLaunch(E.graph[E.cur], E.stream));
       // graph_steps is even: the state ends in the buffers it started in
-      E.launches += (uint64_t)kKernelsPerStep * E.graph_steps;
+      E.launches += (uint64_t)engine_kernels_per_step(E) * E.graph_steps;
       left -= E.graph_steps;
       continue;
     }
@@ -218,10 +226,10 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
     cudaEventRecord(ev[2], E.stream);
     launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
     cudaEventRecord(ev[3], E.stream);
-    launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.n, E.d_ctr, 1, E.force_variant,
-                 E.stream);
+    launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
+                 E.force_variant, E.stream);
     cudaEventRecord(ev[4], E.stream);
-    E.launches += kKernelsPerStep;
+    E.launches += engine_kernels_per_step(E);
     E.cur ^= 1;
     const cudaError_t e = cudaEventSynchronize(ev[4]);
     if (e != cudaSuccess) {
@@ -242,22 +250,57 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
 
 int engine_autotune(Engine& E, int nsteps, double* ms_per_variant, int* chosen) {
   const int nv = force_variants();
-  int best = E.force_variant;
+  // The timing steps must leave no trace: the shapes of the two force algorithms
+  // round differently, so the state and counters are kept and put back afterwards.
+  Arrays keep{};
+  DevCounters* keep_ctr = nullptr;
+  const size_t n = (size_t)E.n;
+  ECU(E, dev_alloc(&keep.pos, n));
+  ECU(E, dev_alloc(&keep.vt, n));
+  ECU(E, dev_alloc(&keep.vel, n));
+  ECU(E, dev_alloc(&keep.frc, n));
+  ECU(E, dev_alloc(&keep_ctr, (size_t)E.nsys));
+  auto copy_state = [&](const Arrays& from, const Arrays& to, const DevCounters* cf, DevCounters* ct) {
+    const size_t b = sizeof(float4) * n;
+    cudaMemcpyAsync(to.pos, from.pos, b, cudaMemcpyDeviceToDevice, E.stream);
+    cudaMemcpyAsync(to.vt, from.vt, b, cudaMemcpyDeviceToDevice, E.stream);
+    cudaMemcpyAsync(to.vel, from.vel, b, cudaMemcpyDeviceToDevice, E.stream);
+    cudaMemcpyAsync(to.frc, from.frc, b, cudaMemcpyDeviceToDevice, E.stream);
+    return cudaMemcpyAsync(ct, cf, sizeof(DevCounters) * E.nsys, cudaMemcpyDeviceToDevice, E.stream);
+  };
+  int rc = DPD_OK;
+  cudaError_t e = copy_state(E.arr[E.cur], keep, E.d_ctr, keep_ctr);
+  if (e != cudaSuccess) rc = engine_fail(E, DPD_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  const int start_variant = E.force_variant;
+  int best = start_variant;
   double best_ms = 1e300;
-  for (int v = 0; v < nv; ++v) {
+  for (int v = 0; v < nv && rc == DPD_OK; ++v) {
     E.force_variant = v;
     double ms[DPD_NPHASES];
-    int rc = engine_time_phases(E, 1, ms);  // warm-up of this shape
+    rc = engine_time_phases(E, 1, ms);  // warm-up of this shape
     if (rc == DPD_OK) rc = engine_time_phases(E, nsteps, ms);
-    if (rc != DPD_OK) return rc;
+    if (rc != DPD_OK) break;
     if (ms_per_variant) ms_per_variant[v] = ms[DPD_PHASE_FORCE];
     if (ms[DPD_PHASE_FORCE] < best_ms) {
       best_ms = ms[DPD_PHASE_FORCE];
       best = v;
     }
   }
-  E.force_variant = best;
+  if (rc == DPD_OK) {
+    e = copy_state(keep, E.arr[E.cur], keep_ctr, E.d_ctr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+    if (e != cudaSuccess) rc = engine_fail(E, DPD_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  } else {
+    cudaStreamSynchronize(E.stream);
+  }
+  cudaFree(keep.pos);
+  cudaFree(keep.vt);
+  cudaFree(keep.vel);
+  cudaFree(keep.frc);
+  cudaFree(keep_ctr);
+  E.force_variant = rc == DPD_OK ? best : start_variant;
   engine_free_graphs(E);
+  if (rc != DPD_OK) return rc;
   if (chosen) *chosen = best;
   return DPD_OK;
 }

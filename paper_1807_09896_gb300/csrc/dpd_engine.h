@@ -15,7 +15,9 @@ namespace dpd {
 
 // Kernels one time step enqueues: counter bump, drift/reflect/key, three scan
 // passes, scatter, per-cell sort, gather, force.
-constexpr int kKernelsPerStep = 9;
+// Kernels of one step: bump, integrate, 3 scan, scatter, cell sort, gather, force
+// (and the force finish for the Newton's-third-law shapes).
+constexpr int kKernelsPerStepBase = 8;
 
 struct Engine {
   int nsys = 0, n = 0, ncells = 0;
@@ -28,6 +30,9 @@ struct Engine {
   DevCounters* d_ctr = nullptr;  // one per system
   DevCounters* h_ctr = nullptr;  // pinned mirror
   cudaStream_t stream = nullptr;
+  // fixed-point pair-force sums of the Newton's-third-law force shapes: 3 per
+  // particle, zero between steps (the finish kernel clears what it reads)
+  unsigned long long* facc = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int use_graph = 1, graph_steps = 20, force_variant = 0;
   uint64_t launches = 0;
@@ -35,6 +40,8 @@ struct Engine {
 };
 
 int engine_fail(Engine& E, int code, const char* fmt, ...);
+// Kernels enqueued per step with the current force shape.
+int engine_kernels_per_step(const Engine& E);
 // Grow buffers to hold nsys systems, n particles and ncells cells (never shrinks).
 int engine_reserve(Engine& E, int nsys, int n, int ncells);
 // Copy the host system table to the device (waits for the copy).

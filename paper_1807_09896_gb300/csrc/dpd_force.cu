@@ -33,7 +33,8 @@ __device__ __forceinline__ float spline_slope(float v) {
 }
 
 // One pair term of Eq. 2 (Eqs. 3-10) for the separation d = r_i - r_j (|d| < r_c):
-// returns (m, e_x, e_y, e_z) with f_ij = m e, e = d / r, w = 1 - r and
+// returns (m, e_x, e_y, e_z) with f_ij = m e, e = d / r, w = 1 - r (solid_pair: one
+// of the two is solid, which selects the fluid-solid coefficients) and
 //   m = C(r) - gamma w^2 (e . (vt_i - vt_j)) + sigma w xi_ij / sqrt(dt),
 // C(r) = a_ij w for force law 0 (Eq. 4) and C(r) = -dE/dr of Eq. 22 for law 1
 // (Eq. 24).  Every force kernel evaluates pairs through this function, so they agree
@@ -41,7 +42,7 @@ __device__ __forceinline__ float spline_slope(float v) {
 template <int kLaw>
 __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float dy, float dz,
                                             float4 vti, const float4* __restrict__ vt, int jj,
-                                            float tagj, uint32_t idi, uint32_t step) {
+                                            float tagj, bool solid_pair, uint32_t idi, uint32_t step) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float inv_r = rsqrtf(r2);
   const float r = r2 * inv_r;
@@ -50,14 +51,13 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
   // a solid neighbour's vt is the wall velocity at its position
   const float4 vtj = __ldg(&vt[jj]);
   if constexpr (kLaw == 0) {
-    const float a = is_solid(tagj) ? P.a_fs : P.a_ff;
+    const float a = solid_pair ? P.a_fs : P.a_ff;
     const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
     const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
     return make_float4(w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi), ex, ey, ez);
   } else {
-    const bool solid = is_solid(tagj);
-    const float kr = solid ? P.sph_kr_fs : P.sph_kr_ff;
-    const float ka = solid ? P.sph_ka_fs : P.sph_ka_ff;
+    const float kr = solid_pair ? P.sph_kr_fs : P.sph_kr_ff;
+    const float ka = solid_pair ? P.sph_ka_fs : P.sph_ka_ff;
     const float c = kr * spline_slope(r * P.sph_ihr) - ka * spline_slope(r * P.sph_iha);
     const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
     const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
@@ -179,7 +179,7 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
       const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
       const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-      const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, idi, step);
+      const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, is_solid(pj.w), idi, step);
       fx = fmaf(t.x, t.y, fx);
       fy = fmaf(t.x, t.z, fy);
       fz = fmaf(t.x, t.w, fz);
@@ -189,6 +189,214 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   }
 
   finish_target(P, A, i, vti, fx, fy, fz, ctr, kick);
+}
+
+// ---------------------------------------------------------------------------
+// Newton's-third-law shapes.  Each unordered pair is evaluated once, by the
+// particle that has the other in its forward half shell: the rest of its own cell
+// (later in cell order), the next cell in x, and the rows (dy, dz) = (+1, 0),
+// (-1, +1), (0, +1), (+1, +1) of three cells each (13 of the 26 neighbour cells; at
+// least three cells per axis make every pair of cells meet once).  The pair force
+// f_ij goes to i and -f_ij (what j computes, bit for bit) to j.  Sums are kept in
+// 64-bit fixed point, 2^32 units per force unit, one array per component (the three
+// atomics of a pair then land in different L2 sectors): integer additions commute, so the
+// result does not depend on the order in which the atomics land and stays bitwise
+// reproducible.  Solid particles take part as the first particle of a pair (their
+// pairs with fluid particles in their half shell) but receive nothing.  A second
+// pass converts the sums, applies the closing half-kick and clears them.
+// ---------------------------------------------------------------------------
+constexpr float kFixScale = 4294967296.0f;  // 2^32
+constexpr float kFixInvF = 1.0f / 4294967296.0f;  // 2^-32
+
+__device__ __forceinline__ void fix_add(unsigned long long* a, float v) {
+  atomicAdd(a, (unsigned long long)__float2ll_rn(v * kFixScale));
+}
+
+// forward rows of the half shell, r = 0..3: (dy, dz) = (+1, 0), (-1, +1), (0, +1), (+1, +1)
+__device__ __forceinline__ void half_row(int r, int* dy, int* dz) {
+  *dy = r == 0 ? 1 : r - 2;
+  *dz = r == 0 ? 0 : 1;
+}
+
+template <int kForceThreads, int kListCap, int kUnroll, int kLaw>
+__device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_t* __restrict__ start,
+                                              const Arrays& A, unsigned long long* __restrict__ facc,
+                                              size_t stride, int i, float4 pi, DevCounters* ctr,
+                                              int (*list)[kForceThreads],
+                                              uint32_t (*seg_b)[kForceThreads],
+                                              uint32_t (*seg_e)[kForceThreads]) {
+  const uint32_t step = ctr->step;
+  const float4 vti = A.vt[i];
+  const bool solid_i = is_solid(pi.w);
+  const uint32_t idi = id_of(pi.w);
+  const float4* __restrict__ pos = A.pos;
+  const float4* __restrict__ vt = A.vt;
+  const int cx = cell_coord(pi.x, P.inv_edge[0], P.nc[0]);
+  const int cy = cell_coord(pi.y, P.inv_edge[1], P.nc[1]);
+  const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
+  const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
+  const bool inner = cx < ncx - 1 && cx > 0;
+  // inner: own tail + next cell (contiguous), then 4 rows of 3 cells; on the x seam:
+  // own tail, next cell, then the 12 row cells one by one
+  const int nseg = inner ? 5 : 14;
+  const int own_row = (cz * ncy + cy) * ncx;
+  if (inner) {
+    // the five ranges' bounds, loaded together up front
+    seg_b[0][threadIdx.x] = (uint32_t)i + 1u;
+    seg_e[0][threadIdx.x] = __ldg(&start[own_row + cx + 2]);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int dy, dz;
+      half_row(r, &dy, &dz);
+      int z = cz + dz, y = cy + dy;
+      z = z >= ncz ? z - ncz : z;
+      y = y < 0 ? y + ncy : (y >= ncy ? y - ncy : y);
+      const int row = (z * ncy + y) * ncx;
+      seg_b[r + 1][threadIdx.x] = __ldg(&start[row + cx - 1]);
+      seg_e[r + 1][threadIdx.x] = __ldg(&start[row + cx + 2]);
+    }
+  }
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  int cnt = 0, seg = 0;
+  uint32_t j = 0, e = 0;
+  float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
+  for (;;) {
+    while (cnt < kListCap) {
+      if (j == e) {
+        if (seg == nseg) break;
+        tx = pi.x; ty = pi.y; tz = pi.z;
+        sx = 0.f; sy = 0.f; sz = 0.f;
+        if (inner && seg == 0) {
+          j = seg_b[0][threadIdx.x];
+          e = seg_e[0][threadIdx.x];
+        } else if (seg == 0) {
+          j = (uint32_t)i + 1u;
+          e = __ldg(&start[own_row + cx + 1]);
+        } else if (!inner && seg == 1) {
+          int x = cx + 1;
+          if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
+          j = __ldg(&start[own_row + x]);
+          e = __ldg(&start[own_row + x + 1]);
+        } else {
+          const int r = inner ? seg - 1 : (seg - 2) / 3;
+          int dy, dz;
+          half_row(r, &dy, &dz);
+          int z = cz + dz, y = cy + dy;
+          if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
+          if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
+          const int row = (z * ncy + y) * ncx;
+          if (inner) {
+            j = seg_b[seg][threadIdx.x];
+            e = seg_e[seg][threadIdx.x];
+          } else {
+            int x = cx + (seg - 2) % 3 - 1;
+            if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
+            j = __ldg(&start[row + x]);
+            e = __ldg(&start[row + x + 1]);
+          }
+        }
+        ++seg;
+        continue;
+      }
+      const uint32_t m = min(min(e - j, 4u), (uint32_t)(kListCap - cnt));
+      float4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < (int)m) q[u] = __ldg(&pos[j + u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < (int)m) {
+          const float dx = tx - (q[u].x - sx);
+          const float dy = ty - (q[u].y - sy);
+          const float dz = tz - (q[u].z - sz);
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < 1.0f && r2 > 0.0f && !(solid_i && is_solid(q[u].w)))
+            list[cnt++][threadIdx.x] = (int)(j + u);
+        }
+      }
+      j += m;
+    }
+#pragma unroll kUnroll
+    for (int k = 0; k < cnt; ++k) {
+      const int jj = list[k][threadIdx.x];
+      const float4 pj = __ldg(&pos[jj]);
+      const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
+      const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
+      const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+      const bool solid_j = is_solid(pj.w);
+      const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, solid_i || solid_j, idi, step);
+      const float gx = t.x * t.y, gy = t.x * t.z, gz = t.x * t.w;
+      fx += gx;
+      fy += gy;
+      fz += gz;
+      if (!solid_j) {
+        fix_add(&facc[jj], -gx);
+        fix_add(&facc[stride + jj], -gy);
+        fix_add(&facc[2 * stride + jj], -gz);
+      }
+    }
+    if (cnt < kListCap) break;  // the cells ran out before the list filled
+    cnt = 0;
+  }
+  if (!solid_i) {
+    fix_add(&facc[i], fx);
+    fix_add(&facc[stride + i], fy);
+    fix_add(&facc[2 * stride + i], fz);
+  }
+  // fixed point cannot carry a NaN or a force beyond its range: flag them here (every
+  // pair this thread evaluated is in its own float sum)
+  const float fmax = fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz)));
+  if (!(fmax < 1.0e9f)) atomicOr(&ctr->status, ST_NAN);
+}
+
+template <int kForceThreads, int kListCap, int kMinBlocks, int kUnroll, bool kBatch, int kLaw>
+__global__ void __launch_bounds__(kForceThreads, kMinBlocks)
+k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
+           const uint32_t* __restrict__ start_all, unsigned long long* __restrict__ facc, int n,
+           DevCounters* ctrs) {
+  __shared__ int list[kListCap][kForceThreads];
+  __shared__ uint32_t seg_b[5][kForceThreads], seg_e[5][kForceThreads];
+  const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 pi = A.pos[i];
+  if constexpr (kBatch) {
+    const int sk = sys_of(S, nsys, (uint32_t)i);
+    force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, A,
+                                                          facc, (size_t)n, i, pi, ctrs + sk, list,
+                                                          seg_b, seg_e);
+  } else {
+    force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, A, facc, (size_t)n, i, pi,
+                                                          ctrs, list, seg_b, seg_e);
+  }
+}
+
+// Second pass: the fixed-point sum becomes the force (one rounding from the exact
+// integer), the closing half-kick is applied and the sum cleared for the next step.
+template <bool kBatch>
+__global__ void __launch_bounds__(256) k_force_finish(StepParams P0, const SysDesc* __restrict__ S,
+                                                      int nsys, Arrays A,
+                                                      unsigned long long* __restrict__ facc, int n,
+                                                      DevCounters* ctrs, int kick) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (is_solid(A.pos[i].w)) return;  // nothing accumulates for solid particles
+  unsigned long long* ax = facc + i;
+  unsigned long long* ay = ax + n;
+  unsigned long long* az = ay + n;
+  // one rounding from the exact integer; the power-of-two scale is exact
+  const float fx = __ll2float_rn((long long)*ax) * kFixInvF;
+  const float fy = __ll2float_rn((long long)*ay) * kFixInvF;
+  const float fz = __ll2float_rn((long long)*az) * kFixInvF;
+  *ax = 0ull;
+  *ay = 0ull;
+  *az = 0ull;
+  const float4 vti = A.vt[i];
+  if constexpr (kBatch) {
+    const int sk = sys_of(S, nsys, (uint32_t)i);
+    finish_target(S[sk].P, A, i, vti, fx, fy, fz, ctrs + sk, kick);
+  } else {
+    finish_target(P0, A, i, vti, fx, fy, fz, ctrs, kick);
+  }
 }
 
 // A single system takes its parameters by value (they stay in the kernel-parameter
@@ -217,15 +425,28 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
 using ForceKernel = void (*)(StepParams, const SysDesc*, int, Arrays, const uint32_t*, int,
                              DevCounters*, int);
 
+using ForceKernelN3 = void (*)(StepParams, const SysDesc*, int, Arrays, const uint32_t*,
+                               unsigned long long*, int, DevCounters*);
+
 struct ForceVariant {
-  ForceKernel single[2], batch[2];  // by force law
+  ForceKernel single[2], batch[2];  // by force law (full-shell shapes)
+  ForceKernelN3 single3[2], batch3[2];  // Newton's-third-law shapes
   int threads;
+  bool n3;
 };
 
 #define DPD_FORCE_VARIANT(T, C, M, U)                                            \
   {                                                                              \
     {k_force<T, C, M, U, false, 0>, k_force<T, C, M, U, false, 1>},              \
-        {k_force<T, C, M, U, true, 0>, k_force<T, C, M, U, true, 1>}, T          \
+        {k_force<T, C, M, U, true, 0>, k_force<T, C, M, U, true, 1>},            \
+        {nullptr, nullptr}, {nullptr, nullptr}, T, false                         \
+  }
+#define DPD_FORCE_VARIANT_N3(T, C, M, U)                                          \
+  {                                                                              \
+    {nullptr, nullptr}, {nullptr, nullptr},                                      \
+        {k_force_n3<T, C, M, U, false, 0>, k_force_n3<T, C, M, U, false, 1>},    \
+        {k_force_n3<T, C, M, U, true, 0>, k_force_n3<T, C, M, U, true, 1>}, T,   \
+        true                                                                     \
   }
 
 static const ForceVariant kForceVariants[] = {
@@ -234,26 +455,45 @@ static const ForceVariant kForceVariants[] = {
     DPD_FORCE_VARIANT(128, 16, 12, 1), DPD_FORCE_VARIANT(256, 12, 6, 1),
     DPD_FORCE_VARIANT(128, 32, 1, 1), DPD_FORCE_VARIANT(128, 24, 1, 2),
     DPD_FORCE_VARIANT(128, 16, 12, 2),
+    DPD_FORCE_VARIANT_N3(128, 12, 1, 1), DPD_FORCE_VARIANT_N3(128, 8, 1, 1),
+    DPD_FORCE_VARIANT_N3(64, 12, 1, 1), DPD_FORCE_VARIANT_N3(256, 8, 1, 1),
+    DPD_FORCE_VARIANT_N3(128, 16, 1, 1),
 };
 
 int force_variants() { return (int)(sizeof(kForceVariants) / sizeof(kForceVariants[0])); }
 
 const char* force_variant_name(int v) {
   static const char* names[] = {"128x24", "128x16", "256x16", "64x24", "128x16/min12",
-                                "256x12/min6", "128x32", "128x24/unroll2", "128x16/min12/unroll2"};
+                                "256x12/min6", "128x32", "128x24/unroll2", "128x16/min12/unroll2",
+                                "n3 128x12", "n3 128x8", "n3 64x12", "n3 256x8", "n3 128x16"};
   return (v >= 0 && v < force_variants()) ? names[v] : "?";
 }
 
+int force_variant_kernels(int variant) {
+  if (variant < 0 || variant >= force_variants()) variant = 0;
+  return kForceVariants[variant].n3 ? 2 : 1;
+}
+
 void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                  const uint32_t* start, int n, DevCounters* ctr, int kick, int variant,
-                  cudaStream_t s) {
+                  const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr, int kick,
+                  int variant, cudaStream_t s) {
   if (n <= 0) return;
   if (variant < 0 || variant >= force_variants()) variant = 0;
   const ForceVariant& fv = kForceVariants[variant];
   const int nb = (n + fv.threads - 1) / fv.threads;
   const int law = P0.law == 1 ? 1 : 0;  // a batch holds systems of one law
-  (nsys == 1 ? fv.single[law] : fv.batch[law])<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, n, ctr,
-                                                                          kick);
+  if (!fv.n3) {
+    (nsys == 1 ? fv.single[law] : fv.batch[law])<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, n,
+                                                                            ctr, kick);
+    return;
+  }
+  (nsys == 1 ? fv.single3[law] : fv.batch3[law])<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, facc,
+                                                                            n, ctr);
+  const int nb2 = (n + 255) / 256;
+  if (nsys == 1)
+    k_force_finish<false><<<nb2, 256, 0, s>>>(P0, S, nsys, A, facc, n, ctr, kick);
+  else
+    k_force_finish<true><<<nb2, 256, 0, s>>>(P0, S, nsys, A, facc, n, ctr, kick);
 }
 
 }  // namespace dpd

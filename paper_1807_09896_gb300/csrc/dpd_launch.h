@@ -15,9 +15,11 @@ void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s);
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s);
 void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                  const uint32_t* start, int n, DevCounters* ctr, int kick, int variant,
-                  cudaStream_t s);
+                  const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr, int kick,
+                  int variant, cudaStream_t s);
 int force_variants();
+// Kernels one launch_force of this shape enqueues (1, or 2 with the finish pass).
+int force_variant_kernels(int variant);
 const char* force_variant_name(int v);
 void launch_profile(const float4* pos, const float4* vel, int n, int axis, int nbins, float lo,
                     float inv_w, double* acc, cudaStream_t s);

@@ -53,6 +53,19 @@ def make_system(w, p: oracle.Params, load=True, **options):
     return s
 
 
+def first_newton3_variant(s) -> int:
+    """Index of the first force launch shape that evaluates each pair once."""
+    keep = int(s.get_option("force_variant"))
+    try:
+        for v in range(int(s.get_option("force_variants"))):
+            s.set_option("force_variant", v)
+            if s.get_option("force_newton3"):
+                return v
+    finally:
+        s.set_option("force_variant", keep)
+    raise AssertionError("no Newton's-third-law force shape")
+
+
 def gpu_state(s):
     pos4, vel4, f4, ids, types = s.state()
     assert np.array_equal(ids, np.arange(len(ids)))

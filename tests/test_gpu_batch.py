@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1807_09896_gb300 import dpd, inputs
-from parity_helpers import compare_one_step, gpu_state, make_system, params_for
+from parity_helpers import compare_one_step, first_newton3_variant, gpu_state, make_system, params_for
 
 pytestmark = pytest.mark.gpu
 
@@ -57,18 +57,41 @@ def test_batched_systems_follow_their_solo_trajectories_bitwise():
 
 
 def test_batch_autotune_and_launch_shapes_keep_trajectories():
+    """Tuning a batch leaves its state as it was; with the chosen shape the members
+    still follow their solo trajectories bit for bit."""
     ws = _small_ensemble(4, seed=7)
     members = _systems(ws)
     b = dpd.Batch([s for s, _ in members])
     chosen, ms = dpd.dpd_batch_autotune(b.hb, 2)
-    steps = int(dpd.dpd_batch_get_stats(b.hb, 0)[7])
-    alone = _systems(ws)
+    assert int(dpd.dpd_batch_get_stats(b.hb, 0)[7]) == 0
+    b.step(12)
+    alone = _systems(ws)  # loaded (f(0)) with the default shape, as the members were
     for s, _ in alone:
-        s.step(steps)
+        s.set_option("force_variant", chosen)
+        s.step(12)
     for k, (s, _) in enumerate(alone):
         for x, y in zip(gpu_state(s), _batch_state(b, k)):
             np.testing.assert_array_equal(x, y)
     assert 0 <= chosen < len(ms)
+    b.close()
+
+
+def test_newton3_batch_members_follow_their_solo_trajectories_bitwise():
+    """Fixed-point sums do not depend on the order of the atomics, so a member of a
+    batch using the Newton's-third-law force shapes matches its solo run bit for bit."""
+    ws = _small_ensemble(5, seed=9)
+    probe = _systems(ws[:1])[0][0]
+    v3 = first_newton3_variant(probe)
+    alone = _systems(ws)  # loaded (f(0)) with the default shape, as the members were
+    for s, _ in alone:
+        s.set_option("force_variant", v3)
+        s.step(17)
+    members = _systems(ws)
+    b = dpd.Batch([s for s, _ in members], force_variant=v3, graph_steps=8)
+    b.step(17)
+    for k, (s, _) in enumerate(alone):
+        for x, y in zip(gpu_state(s), _batch_state(b, k)):
+            np.testing.assert_array_equal(x, y)
     b.close()
 
 

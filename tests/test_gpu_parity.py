@@ -14,7 +14,8 @@ import pytest
 
 import oracle
 from paper_1807_09896_gb300 import dpd, inputs
-from parity_helpers import (check_forces, compare_one_step, force_scales, gpu_state,
+from parity_helpers import (check_forces, compare_one_step, first_newton3_variant, force_scales,
+                            gpu_state,
                             make_system, params_for)
 
 pytestmark = pytest.mark.gpu
@@ -34,8 +35,10 @@ def _field(w):
     return oracle.Field(w.phi, w.h)
 
 
-def _initial_force_parity(w, p):
-    s = make_system(w, p)
+def _initial_force_parity(w, p, newton3=False):
+    s = make_system(w, p, load=False)
+    _use_algorithm(s, newton3)
+    s.set_particles(w.pos4(), w.vel4(), w.id, w.type)
     pos, vel, frc, types = gpu_state(s)
     ids = np.arange(len(pos))
     vt = vel.astype(np.float64)
@@ -58,20 +61,28 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("newton3", [False, True])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_initial_force_matches_oracle(name):
+def test_initial_force_matches_oracle(name, newton3):
     w = CASES[name]()
     p = params_for(w, g=(0.02, 0.0, 0.0), seed=123)
-    s, err = _initial_force_parity(w, p)
+    s, err = _initial_force_parity(w, p, newton3)
     assert err < 1e-5
     s.close()
 
 
+def _use_algorithm(s, newton3):
+    s.set_option("force_variant", first_newton3_variant(s) if newton3 else 0)
+    assert bool(s.get_option("force_newton3")) == newton3
+
+
+@pytest.mark.parametrize("newton3", [False, True])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_steps_match_oracle_from_identical_state(name):
+def test_steps_match_oracle_from_identical_state(name, newton3):
     w = CASES[name]()
     p = params_for(w, g=(0.02, 0.0, 0.0), seed=7)
     s = make_system(w, p)
+    _use_algorithm(s, newton3)
     field = _field(w)
     seen_reflections = 0
     for block in range(4):
@@ -235,13 +246,14 @@ def test_no_fluid_particle_enters_the_solid_over_a_run():
     s.close()
 
 
-def test_full_size_channel_one_million():
+@pytest.mark.parametrize("newton3", [False, True])
+def test_full_size_channel_one_million(newton3):
     """The benchmark's workload (channel 80 x 64 x 64 gap, ~983k fluid particles)
     in the benchmark's launch configuration (graph replay): after 20 graph steps
     one more step is compared particle by particle with the oracle."""
     w = inputs.channel(80.0, 64.0, 64.0, seed=0)
     p = params_for(w, g=(0.01, 0.0, 0.0), seed=0)
-    s, err = _initial_force_parity(w, p)
+    s, err = _initial_force_parity(w, p, newton3)
     s.set_option("use_graph", 1)
     s.set_option("graph_steps", 20)
     s.step(20)
@@ -251,33 +263,50 @@ def test_full_size_channel_one_million():
 
 
 def test_every_force_launch_shape_gives_bitwise_identical_steps():
+    """Within each force algorithm every launch shape gives the same bits; the two
+    algorithms (full shell in binary32, Newton's third law in fixed point) agree to
+    rounding."""
     w = inputs.channel(9.0, 7.0, 6.0, seed=16)
     p = params_for(w, g=(0.02, 0, 0), seed=6)
-    ref = None
+    ref, f0 = {}, {}
     nv = int(make_system(w, p, load=False).get_option("force_variants"))
     for v in range(nv):
         s = make_system(w, p, load=False, force_variant=v)
+        fam = bool(s.get_option("force_newton3"))
         s.set_particles(w.pos4(), w.vel4(), w.id, w.type)
+        f0.setdefault(fam, gpu_state(s)[2])
         s.step(7)
         st = gpu_state(s)
-        if ref is None:
-            ref = st
+        if fam not in ref:
+            ref[fam] = st
         else:
-            for x, y in zip(ref, st):
+            for x, y in zip(ref[fam], st):
                 np.testing.assert_array_equal(x, y)
         s.close()
+    assert set(ref) == {False, True}
+    # from the same state the two algorithms' forces differ by the rounding of the sums
+    assert np.abs(f0[False] - f0[True]).max() < 1e-4
 
 
 def test_autotune_keeps_results_and_picks_a_shape():
+    """Tuning leaves the state and counters as they were; afterwards the system
+    steps like any system using the chosen shape."""
     w = inputs.channel(10.0, 8.0, 6.0, seed=17)
     p = params_for(w, seed=8)
     a = make_system(w, p)
     b = make_system(w, p)
+    before = gpu_state(a), a.stats()
     chosen, ms = dpd.dpd_autotune(a.h, 2)
     assert 0 <= chosen < len(ms) and all(m > 0 for m in ms)
     assert a.get_option("force_variant") == chosen
-    steps_done = int(a.get_option("step"))
-    b.step(steps_done)
+    for x, y in zip(before[0], gpu_state(a)):
+        np.testing.assert_array_equal(x, y)
+    after = a.stats()
+    np.testing.assert_array_equal(before[1][5:], after[5:])  # reflections, fallbacks, step
+    np.testing.assert_allclose(before[1][:5], after[:5], rtol=1e-12)  # FP64 atomic sums
+    b.set_option("force_variant", chosen)
+    a.step(9)
+    b.step(9)
     for x, y in zip(gpu_state(a), gpu_state(b)):
         np.testing.assert_array_equal(x, y)
 
