@@ -64,6 +64,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint and precision lines")
+    ap.add_argument("--force-variant", type=int, default=-1,
+                    help="use this pair-force launch shape instead of tuning (e.g. to profile it)")
     ap.add_argument("--batched-steps", type=int, default=200)
     return ap.parse_args()
 
@@ -427,8 +429,13 @@ def run_ours(args):
             dist.barrier()
 
     s.step(args.warmup)
-    # pick the pair-force launch shape on this device (all shapes are bit-identical)
-    chosen, _ = dpd.dpd_autotune(s.h, 5)
+    # pick the pair-force launch shape on this device (tuning leaves the state as it was)
+    if args.force_variant >= 0:
+        s.set_option("force_variant", args.force_variant)
+        chosen = args.force_variant
+    else:
+        chosen, _ = dpd.dpd_autotune(s.h, 5)
+    newton3 = bool(s.get_option("force_newton3"))
     s.step(2)
     torch.cuda.synchronize(dev)
     launches0 = s.get_option("kernel_launches")
@@ -459,14 +466,17 @@ def run_ours(args):
     nph = min(args.steps, 50)
     ph = dpd.dpd_time_phases(s.h, nph)
     force_ms = ph["force"]
-    cand = 27 * 3.0                 # 27 cells of unit volume at rho = 3
-    pairs = 4.0 / 3.0 * math.pi * 3.0  # neighbours within r_c at rho = 3
+    # the chosen algorithm's own work: the full shell tests 27 cells and evaluates every
+    # pair from both sides; the half shell tests 13.5 cells and each pair once
+    cells = 13.5 if newton3 else 27.0
+    cand = cells * 3.0                 # cells of unit volume at rho = 3
+    pairs = cells / 27.0 * 4.0 / 3.0 * math.pi * 3.0  # partners within r_c at rho = 3
     ops_per_launch = w.n_fluid * (cand * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR)
     achieved_tops = ops_per_launch / (force_ms / 1e3) / 1e12
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
     peak_tops = sm_count * LANES_PER_SM * max_mhz * 1e6 / 1e12
-    traffic = _force_traffic()
+    traffic = (_force_traffic() or {}).get("variants", {}).get(str(chosen))
     hbm_peak, hbm_src, _ = _peaks()
     step_gbs = BYTES_PER_PARTICLE_STEP * (w.n_fluid + w.n_solid) * args.steps / (ms / 1e3) / 1e9
 
@@ -524,7 +534,11 @@ def run_ours(args):
                 "force_launch_shape": chosen,
             },
             "roofline": {
-                "kernel": "k_force (pair force + closing half-kick)", "bound": "alu",
+                "kernel": ("k_force_n3 + k_force_finish (half-shell pair force, fixed-point sums, "
+                           "closing half-kick)" if newton3 else
+                           "k_force (full-shell pair force + closing half-kick)"),
+                "bound": "alu",
+                "ops_per_particle": cand * OPS_PER_CANDIDATE + pairs * OPS_PER_PAIR,
                 "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved_tops / peak_tops,
                 "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {max_mhz:g} MHz",
