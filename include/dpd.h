@@ -94,6 +94,20 @@ int dpd_create(dpd_t** h, const double box[3], double rho, const double a_ij[4],
  * (no reflection).  Must precede dpd_set_particles. */
 int dpd_set_phase_field(dpd_t* h, const float* grid, const int dims[3], double spacing);
 
+/* Set up particles from the phase field as Sec. II.C describes: a dense random
+ * fluid at the create-time density rho fills the whole box, and the interpolated
+ * phase field (set first; without one every site is fluid) classifies each site:
+ * phi >= 0 fluid, phi_min < phi < 0 frozen solid, phi <= phi_min removed, with
+ * phi_min = tanh(-solid_layer / (sqrt(2) eps)) the value of Eq. 14 at a distance
+ * solid_layer inside the solid (eps: option "phase_eps", default 0.5).  Site k of
+ * round(rho Lx Ly Lz) takes its position from Philox4x32-10 of the counter
+ * (k, 0xFFFFFFFF, 0xFFFFFFFE, system) and a Maxwellian velocity at kBT (Box-Muller)
+ * from (k, 0xFFFFFFFF, 0xFFFFFFFD, system), key = seed; the mean fluid velocity is
+ * removed; kept sites get ids 0..n-1 in site order.  Deterministic.  Then loads the
+ * particles as dpd_set_particles does (errors likewise; DPD_EOVERFLOW if
+ * rho V >= 2^30, DPD_EINVAL if solid_layer < 0). */
+int dpd_init_particles(dpd_t* h, uint64_t seed, double solid_layer);
+
 /* Load n particles (any order): pos4 positions (wrapped into the box), vel4
  * velocities, id a permutation of 0..n-1, type 0 fluid / 1 solid.  Computes the
  * pair force f(0) at the given state (predicted velocity = v).  Solid
@@ -212,7 +226,8 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * displacement of the step, 1: v(t) dt as printed in Eq. 17), "seed" (integer
  * <= 2^53), "system" (Philox counter word 3), "v_wall_x|y|z", "shear_x|y|z",
  * "shear_axis" (0-2, default 2), "shear_ref" (the wall velocity field above; a
- * shear component along shear_axis is DPD_EINVAL), "force_law" (0: the soft
+ * shear component along shear_axis is DPD_EINVAL), "phase_eps" (eps of Eq. 14 for
+ * dpd_init_particles, default 0.5), "force_law" (0: the soft
  * repulsion a_ij w of Eq. 4; 1: the attractive/repulsive pair energy of Eq. 22,
  * E = S^r W(r, r0^r) - S^a W(r, r0^a) with the cubic spline W of Eq. 23, whose
  * conservative force is -dE/dr along r_ij (Eq. 24); the dissipative and random

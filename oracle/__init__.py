@@ -83,6 +83,10 @@ def lib() -> ctypes.CDLL:
             getattr(L, fn).restype = ctypes.c_double
         L.or_sph_energy.argtypes = [f64p, ctypes.c_double, ctypes.c_int]
         L.or_sph_energy.restype = ctypes.c_double
+        L.or_init_particles.argtypes = [ctypes.c_long, f64p, ctypes.c_double, ctypes.c_uint64,
+                                        ctypes.c_uint32, ctypes.c_double, ctypes.c_int, f32p, i32p,
+                                        ctypes.c_double, f64p, u8p, f64p, f64p, u8p, i64p]
+        L.or_init_particles.restype = ctypes.c_long
         L.or_profile.argtypes = [ctypes.c_int, f32p, f64p, u8p, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double, ctypes.c_double, f64p]
         L.or_profile.restype = None
@@ -265,6 +269,28 @@ def sph_dWdr(r: float, r0: float, D: int) -> float:
 def sph_energy(p: Params, r: float, fluid_solid: bool = False) -> float:
     """Pair energy of Eq. 22 with the strengths of p."""
     return lib().or_sph_energy(p.flat(), float(r), int(bool(fluid_solid)))
+
+
+def init_particles(box, rho: float, kBT: float, seed: int, phi_min: float, field=None, sys: int = 0):
+    """Particle set-up from the phase field (Sec. II.C): round(rho V) random sites,
+    classified by phi (fluid >= 0 > solid > phi_min >= removed), mean fluid velocity
+    removed.  Returns a dict: pos, vel, type, site (kept particles in site order) and
+    site_phi, site_type (every site)."""
+    L = np.asarray(box, np.float64)
+    n0 = int(np.floor(rho * L.prod() + 0.5))
+    m = max(n0, 1)
+    site_phi = np.zeros(m); site_type = np.zeros(m, np.uint8)
+    pos = np.zeros((m, 3)); vel = np.zeros((m, 3)); typ = np.zeros(m, np.uint8)
+    site = np.zeros(m, np.int64)
+    if field is None:
+        grid, dims, h, have = np.ones(1, np.float32), np.ones(3, np.int32), 1.0, 0
+    else:
+        grid, dims, h, have = _c(field.grid, np.float32).reshape(-1), field.dims, field.h, 1
+    n = lib().or_init_particles(n0, _c(L, np.float64), float(kBT), int(seed), int(sys), float(phi_min),
+                                have, grid, dims, float(h), site_phi, site_type, pos.reshape(-1),
+                                vel.reshape(-1), typ, site)
+    return {"pos": pos[:n], "vel": vel[:n], "type": typ[:n], "site": site[:n],
+            "site_phi": site_phi[:n0], "site_type": site_type[:n0], "n0": n0}
 
 
 def wall_velocities(pos, types, p: Params) -> np.ndarray:

@@ -62,6 +62,11 @@
  *       strengths (the paper doubles the fluid-fluid ones); the dissipative
  *       and random parts keep the weights of Eqs. 5-8 with r_c = 1, so both
  *       ranges must be <= 1.
+ *   R20 set-up (Sec. II.C): a dense random fluid at the density rho fills the
+ *       box, and the phase field classifies it -- fluid where phi >= 0, frozen
+ *       solid where phi_min < phi < 0, removed deeper; phi_min is the value of
+ *       Eq. 14 at the chosen solid-layer depth.  Positions and velocities come
+ *       from Philox4x32-10 streams disjoint from the pair noise.
  */
 #include <math.h>
 #include <stdint.h>
@@ -607,4 +612,61 @@ int or_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Particle set-up from the phase field (Sec. II.C, reading R20).       */
+/* A dense random fluid fills the box: site k of n0 (= round(rho V),    */
+/* given by the caller) takes its position from Philox4x32-10 of the    */
+/* counter (k, 0xFFFFFFFF, 0xFFFFFFFE, sys) and a Maxwellian velocity   */
+/* from (k, 0xFFFFFFFF, 0xFFFFFFFD, sys), key = seed:                   */
+/*   r = (u0 Lx, u1 Ly, u2 Lz),                                         */
+/*   v = sqrt(kBT) (sqrt(-2 ln u0') cos(2 pi u1'),                      */
+/*                  sqrt(-2 ln u0') sin(2 pi u1'),                      */
+/*                  sqrt(-2 ln u2') cos(2 pi u3')).                     */
+/* The interpolated phase field classifies every site: phi >= 0 fluid,  */
+/* phi_min < phi < 0 frozen solid, otherwise removed.  The mean fluid   */
+/* velocity is subtracted.  Kept sites are numbered in site order.      */
+/* Outputs: site_phi[n0], site_type[n0] (0 fluid, 1 solid, 2 removed),  */
+/* and the kept particles pos, vel (n x 3), type (n), site (n).         */
+/* Returns n.  have_grid = 0 means phi = +1 everywhere.                 */
+/* ------------------------------------------------------------------ */
+long or_init_particles(long n0, const double L[3], double kBT, uint64_t seed, uint32_t sys,
+                       double phi_min, int have_grid, const float* grid, const int* dims, double h,
+                       double* site_phi, uint8_t* site_type, double* pos, double* vel, uint8_t* type,
+                       long* site) {
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  long n = 0, nf = 0;
+  double mean[3] = {0.0, 0.0, 0.0};
+  for (long k = 0; k < n0; ++k) {
+    uint32_t ca[4] = {(uint32_t)k, 0xFFFFFFFFu, 0xFFFFFFFEu, sys}, wa[4];
+    uint32_t cb[4] = {(uint32_t)k, 0xFFFFFFFFu, 0xFFFFFFFDu, sys}, wb[4];
+    or_philox4x32_10(ca, key, wa);
+    or_philox4x32_10(cb, key, wb);
+    const double r[3] = {or_u01(wa[0]) * L[0], or_u01(wa[1]) * L[1], or_u01(wa[2]) * L[2]};
+    const double ra = sqrt(-2.0 * log(or_u01(wb[0]))), rb = sqrt(-2.0 * log(or_u01(wb[2])));
+    const double s = sqrt(kBT);
+    const double v[3] = {s * ra * cos(2.0 * M_PI * or_u01(wb[1])), s * ra * sin(2.0 * M_PI * or_u01(wb[1])),
+                         s * rb * cos(2.0 * M_PI * or_u01(wb[3]))};
+    const double phi = have_grid ? or_phi_at(grid, dims, h, r[0], r[1], r[2]) : 1.0;
+    const uint8_t t = phi >= 0.0 ? 0 : (phi > phi_min ? 1 : 2);
+    site_phi[k] = phi;
+    site_type[k] = t;
+    if (t == 2) continue;
+    for (int a = 0; a < 3; ++a) {
+      pos[3 * n + a] = r[a];
+      vel[3 * n + a] = t == 0 ? v[a] : 0.0;
+    }
+    if (t == 0) {
+      for (int a = 0; a < 3; ++a) mean[a] += v[a];
+      ++nf;
+    }
+    type[n] = t;
+    site[n] = k;
+    ++n;
+  }
+  for (long i = 0; i < n; ++i)
+    if (type[i] == 0)
+      for (int a = 0; a < 3; ++a) vel[3 * i + a] -= mean[a] / (double)nf;
+  return n;
 }

@@ -495,6 +495,9 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     h->shear_axis = (int)v;
   } else if (k == "shear_ref") {
     h->shear_ref = v;
+  } else if (k == "phase_eps") {
+    if (!(v > 0.0)) return fail(h, DPD_EINVAL, "phase_eps must be > 0");
+    h->phase_eps = v;
   } else if (k == "force_law") {
     if (v != 0.0 && v != 1.0) return fail(h, DPD_EINVAL, "force_law must be 0 or 1");
     h->force_law = (int)v;
@@ -553,6 +556,7 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "shear_axis") *v = h->shear_axis;
   else if (k == "shear_ref") *v = h->shear_ref;
   else if (k == "force_law") *v = h->force_law;
+  else if (k == "phase_eps") *v = h->phase_eps;
   else if (k == "S_r_ff" || k == "S_a_ff" || k == "S_r_fs" || k == "S_a_fs")
     *v = h->sph_S[(k[5] == 's' ? 2 : 0) + (k[2] == 'a' ? 1 : 0)];
   else if (k == "r0_r" || k == "r0_a") *v = h->sph_r0[k[3] == 'a' ? 1 : 0];

@@ -174,9 +174,10 @@ __device__ __forceinline__ float two_sum(float a, float b, float* err) {
 // counter (min id, max id, step, system) under the key (seed_lo, seed_hi); the
 // first two output words become two uniforms u = ((w >> 9) + 1/2) 2^-23, exact in
 // binary32, and the Box-Muller transform gives xi = sqrt(-2 ln u0) cos(2 pi u1).
-__device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t step, uint32_t sys,
-                                            uint32_t k0, uint32_t k1) {
-  uint32_t c0 = min(ida, idb), c1 = max(ida, idb), c2 = step, c3 = sys;
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds on the counter (c0..c3) under the
+// key (k0, k1); the result replaces the counter.
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                              uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
@@ -188,6 +189,17 @@ __device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
+}
+
+// Uniform in (0, 1) from one output word: ((w >> 9) + 1/2) 2^-23, exact in binary32.
+__device__ __forceinline__ float philox_u01(uint32_t w) {
+  return (__uint2float_rn(w >> 9) + 0.5f) * 0x1p-23f;
+}
+
+__device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t step, uint32_t sys,
+                                            uint32_t k0, uint32_t k1) {
+  uint32_t c0 = min(ida, idb), c1 = max(ida, idb), c2 = step, c3 = sys;
+  philox4x32_10(c0, c1, c2, c3, k0, k1);
   const float u0 = (__uint2float_rn(c0 >> 9) + 0.5f) * 0x1p-23f;
   const float u1 = (__uint2float_rn(c1 >> 9) + 0.5f) * 0x1p-23f;
   // cos(2 pi u1) = -cos(2 pi u1 - pi), evaluated by the hardware cosine on an

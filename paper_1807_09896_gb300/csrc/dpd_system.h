@@ -27,6 +27,7 @@ struct dpd_system {
   double sph_r0[2] = {0.73, 1.0};               // r0^r, r0^a
   int sph_dim = 3;
   double margin = 0.5;
+  double phase_eps = 0.5;  // interface parameter eps of Eq. 14 (used by dpd_init_particles)
   uint64_t seed = 0;
   uint32_t sys = 0;
   int reflect_variant = 0;

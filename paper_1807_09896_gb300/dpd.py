@@ -41,6 +41,7 @@ _SIGS = {
     "dpd_velocity_profile": (_i, [_vp, _i, _i, _d, _d, _vp, _i]),
     "dpd_velocity_profile_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _vp, _i, _vp]),
     "dpd_relax_phase_field": (_i, [_vp, _vp, _d, _d, _i, _d, _i, _vp]),
+    "dpd_init_particles": (_i, [_vp, ctypes.c_uint64, _d]),
     "dpd_get_stats": (_i, [_vp, _vp]),
     "dpd_set_option": (_i, [_vp, ctypes.c_char_p, _d]),
     "dpd_get_option": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_d)]),
@@ -212,6 +213,11 @@ def dpd_velocity_profile(h, axis: int, nbins: int, lo: float, hi: float, mode: i
     return out
 
 
+def dpd_init_particles(h, seed, solid_layer=1.0):
+    """Random fluid at rho over the box, classified by the phase field (Sec. II.C)."""
+    return _check(h, load_library().dpd_init_particles(h, int(seed), float(solid_layer)))
+
+
 def dpd_relax_phase_field(phi, spacing, eps, iters, dtau, curvature=True):
     """Relax a phase field (float32 array (nz, ny, nx)) by Eq. 15 (curvature=True) or
     Eq. 13; returns (new array, mean ms per step)."""
@@ -289,6 +295,9 @@ class System:
         if set_particles:
             s.set_particles(w.pos4(), w.vel4(), w.id, w.type)
         return s
+
+    def init_particles(self, seed, solid_layer=1.0):
+        return dpd_init_particles(self.h, seed, solid_layer)
 
     def set_particles(self, pos4, vel4, ids, types, where=DPD_HOST):
         return dpd_set_particles(self.h, pos4, vel4, ids, types, where)
