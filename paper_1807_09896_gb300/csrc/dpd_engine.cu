@@ -143,7 +143,7 @@ void engine_enqueue_sort(Engine& E) {
 }
 
 int engine_kernels_per_step(const Engine& E) {
-  return kKernelsPerStepBase + force_variant_kernels(E.force_variant);
+  return kKernelsPerStepBase + scan_kernels(E.ncells) + force_variant_kernels(E.force_variant);
 }
 
 void engine_enqueue_force(Engine& E, int kick) {

@@ -15,9 +15,9 @@ namespace dpd {
 
 // Kernels one time step enqueues: counter bump, drift/reflect/key, three scan
 // passes, scatter, per-cell sort, gather, force.
-// Kernels of one step: bump, integrate, 3 scan, scatter, cell sort, gather, force
-// (and the force finish for the Newton's-third-law shapes).
-constexpr int kKernelsPerStepBase = 8;
+// Kernels of one step besides the scan and the force: bump, integrate, scatter, cell
+// sort, gather.
+constexpr int kKernelsPerStepBase = 5;
 
 struct Engine {
   int nsys = 0, n = 0, ncells = 0;

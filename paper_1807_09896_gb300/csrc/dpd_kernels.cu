@@ -109,7 +109,19 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
   }
   const uint32_t c = cell_off + (uint32_t)cell_of(P, p.x, p.y, p.z);
   C.key[i] = c;
-  C.rank[i] = atomicAdd(&C.count[c], 1u);
+  // Arrival slot in the cell.  Neighbouring threads mostly hold particles of the same
+  // cell (the arrays are in cell order from the previous step), so the lanes of a warp
+  // that share a cell take their slots with one atomic: the group's lowest lane adds
+  // the group size and each lane takes base + its rank in the group.  (The per-cell id
+  // order of the sort fixes the final order, so the slots' order does not matter.)
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, c);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&C.count[c], (uint32_t)__popc(peers));
+  base = __shfl_sync(active, base, leader);
+  C.rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
 // A single system takes its parameters by value (kernel-parameter bank); a batch
@@ -203,6 +215,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* blocksum, i
   }
 }
 
+// Few blocks: each block sums the totals of the blocks before it itself (at most
+// kScanFuseMax values), so no separate pass scans the totals.
+constexpr int kScanFuseMax = 1024;
+
+template <bool kOwnOffset>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* count, int m,
                                                             const uint32_t* blocksum,
                                                             uint32_t* start, uint32_t n_total) {
@@ -214,8 +231,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* count, int
     v[k] = (base + k < m) ? count[base + k] : 0u;
     s += v[k];
   }
-  uint32_t tot;
-  uint32_t run = blocksum[blockIdx.x] + block_excl_scan(s, &tot);
+  uint32_t tot, off;
+  if constexpr (kOwnOffset) {
+    uint32_t part = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += kScanThreads) part += blocksum[j];
+    block_excl_scan(part, &off);
+  } else {
+    off = blocksum[blockIdx.x];
+  }
+  uint32_t run = off + block_excl_scan(s, &tot);
 #pragma unroll
   for (int k = 0; k < kScanPerThread; ++k) {
     if (base + k < m) {
@@ -478,11 +502,17 @@ void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, 
 
 int scan_blocks(int ncells) { return blocks(ncells, kScanChunk); }
 
+int scan_kernels(int ncells) { return scan_blocks(ncells) <= kScanFuseMax ? 2 : 3; }
+
 void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s) {
   const int nb = scan_blocks(ncells);
   k_scan_reduce<<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum);
-  k_scan_top<<<1, kScanThreads, 0, s>>>(C.blocksum, nb);
-  k_scan_down<<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum, C.start, (uint32_t)n);
+  if (nb <= kScanFuseMax) {
+    k_scan_down<true><<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum, C.start, (uint32_t)n);
+  } else {
+    k_scan_top<<<1, kScanThreads, 0, s>>>(C.blocksum, nb);
+    k_scan_down<false><<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum, C.start, (uint32_t)n);
+  }
 }
 
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,

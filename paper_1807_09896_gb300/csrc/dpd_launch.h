@@ -11,6 +11,8 @@ void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Ar
 void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
                 cudaStream_t s);
 int scan_blocks(int ncells);
+// Kernels one launch_scan enqueues (2 for up to 1024 scan blocks, else 3).
+int scan_kernels(int ncells);
 void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s);
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s);
