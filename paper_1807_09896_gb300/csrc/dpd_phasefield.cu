@@ -85,6 +85,46 @@ __device__ __forceinline__ PlaneTerms plane_terms(const float* slot, int row, in
   return t;
 }
 
+// New value of the thread's two nodes of plane k from the terms of planes k-1, k, k+1
+// (the right-hand side written out in raw differences, see k_relax).
+template <bool kCurvature>
+__device__ __forceinline__ float2 node_update(const PlaneTerms& prev, const PlaneTerms& cur,
+                                              const PlaneTerms& nxt, float inv2, float dprime,
+                                              float dtau) {
+  const float2 p = cur.p;
+  const float2 dz = sub2(nxt.p, prev.p);
+  const float2 sxx = fma2(splat(-2.0f), p, cur.xs);
+  const float2 syy = fma2(splat(-2.0f), p, cur.ys);
+  const float2 szz = fma2(splat(-2.0f), p, add2(nxt.p, prev.p));
+  const float2 lap = add2(add2(sxx, syy), szz);
+  const float2 reaction = fma2(mul2(p, p), make_float2(-p.x, -p.y), p);
+  float2 q = lap;
+  if (kCurvature) {
+    const float2 dx = cur.dx, dy = cur.dy;
+    const float2 sxz = sub2(nxt.dx, prev.dx), syz = sub2(nxt.dy, prev.dy);
+    const float2 G = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, splat(dprime))));
+    float2 N = mul2(mul2(dz, szz), dz);
+    N = fma2(mul2(dy, syy), dy, N);
+    N = fma2(mul2(dx, sxx), dx, N);
+    const float2 m1 = fma2(dz, sxz, mul2(dy, cur.sxy));
+    const float2 M = fma2(dx, m1, mul2(dy, mul2(dz, syz)));
+    N = fma2(splat(0.5f), M, N);
+    const float2 num = fma2(splat(dprime), lap, N);
+    q = make_float2(__fdividef(num.x, G.x), __fdividef(num.y, G.y));  // G >= d' > 0
+  }
+  const float2 rhs = fma2(splat(inv2), q, reaction);
+  return fma2(splat(dtau), rhs, p);
+}
+
+__device__ __forceinline__ void store_pair(float* dst, float2 o, int i, int nx, int pair_store) {
+  if (pair_store) {
+    *reinterpret_cast<float2*>(dst) = o;  // i even and nx even: 8-byte aligned, i + 1 < nx
+  } else {
+    dst[0] = o.x;
+    if (i + 1 < nx) dst[1] = o.y;
+  }
+}
+
 // 2.5-D blocked stencil.  Each block streams planes k0-1 .. k0+KZ (periodic) through
 // a ring of halo'd shared-memory slots filled kAhead planes ahead by cp.async, and
 // carries the per-plane terms of planes k-1, k, k+1 in registers; the plane loop has
@@ -149,37 +189,8 @@ __global__ void __launch_bounds__(TX * TY) k_relax(const float* __restrict__ phi
     __syncthreads();       // ... for every thread's copies
     const PlaneTerms nxt = plane_terms(ring[s & (kRing - 1)], row, col);
     if (s >= 2) {
-      if (active && k0 + s - 2 < nz) {  // node plane k = k0 + s - 2
-        const float2 p = cur.p;
-        const float2 dz = sub2(nxt.p, prev.p);
-        const float2 sxx = fma2(splat(-2.0f), p, cur.xs);
-        const float2 syy = fma2(splat(-2.0f), p, cur.ys);
-        const float2 szz = fma2(splat(-2.0f), p, add2(nxt.p, prev.p));
-        const float2 lap = add2(add2(sxx, syy), szz);
-        const float2 reaction = fma2(mul2(p, p), make_float2(-p.x, -p.y), p);
-        float2 q = lap;
-        if (kCurvature) {
-          const float2 dx = cur.dx, dy = cur.dy;
-          const float2 sxz = sub2(nxt.dx, prev.dx), syz = sub2(nxt.dy, prev.dy);
-          const float2 G = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, splat(dprime))));
-          float2 N = mul2(mul2(dz, szz), dz);
-          N = fma2(mul2(dy, syy), dy, N);
-          N = fma2(mul2(dx, sxx), dx, N);
-          const float2 m1 = fma2(dz, sxz, mul2(dy, cur.sxy));
-          const float2 M = fma2(dx, m1, mul2(dy, mul2(dz, syz)));
-          N = fma2(splat(0.5f), M, N);
-          const float2 num = fma2(splat(dprime), lap, N);
-          q = make_float2(__fdividef(num.x, G.x), __fdividef(num.y, G.y));  // G >= d' > 0
-        }
-        const float2 rhs = fma2(splat(inv2), q, reaction);
-        const float2 o = fma2(splat(dtau), rhs, p);
-        if (pair_store) {
-          *reinterpret_cast<float2*>(dst) = o;  // i even and nx even: 8-byte aligned, i + 1 < nx
-        } else {
-          dst[0] = o.x;
-          if (i + 1 < nx) dst[1] = o.y;
-        }
-      }
+      if (active && k0 + s - 2 < nz)  // node plane k = k0 + s - 2
+        store_pair(dst, node_update<kCurvature>(prev, cur, nxt, inv2, dprime, dtau), i, nx, pair_store);
       dst += plane;
     }
     prev = cur;
@@ -187,6 +198,7 @@ __global__ void __launch_bounds__(TX * TY) k_relax(const float* __restrict__ phi
   }
   wait_async<0>();
 }
+
 
 }  // namespace
 
