@@ -270,7 +270,8 @@ __global__ void k_scatter(CellList C, int n, DevCounters* ctr) {
 }
 
 // One thread per cell: put the cell's entries of perm in ascending particle id
-// order (insertion sort; cells hold a handful of particles).  This makes the
+// order (insertion sort; cells hold a handful of particles, and up to 8 are sorted in
+// registers, the rest through a local array).  This makes the
 // order of every later floating-point sum independent of atomic timing.
 constexpr int kCellSortCap = 48;
 
@@ -282,6 +283,32 @@ __global__ void k_cell_sort(CellList C, const float4* pos, int n, int ncells, De
   if (m <= 1) return;
   if (m > kCellSortCap) {
     atomicOr(&ctr->status, ST_OVERFLOW);
+    return;
+  }
+  if (m <= 8) {
+    // small cell (nearly all): sort in registers, fully unrolled
+    uint32_t ri[8], rk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      ri[k] = 0u;
+      rk[k] = 0xFFFFFFFFu;
+      if (k < m) {
+        ri[k] = min(C.perm[b + k], (uint32_t)(n - 1));
+        rk[k] = id_of(pos[ri[k]].w);
+      }
+    }
+#pragma unroll
+    for (int a = 1; a < 8; ++a)
+#pragma unroll
+      for (int q = a; q > 0; --q)
+        if (rk[q - 1] > rk[q]) {
+          const uint32_t tk = rk[q - 1], ti = ri[q - 1];
+          rk[q - 1] = rk[q]; ri[q - 1] = ri[q];
+          rk[q] = tk; ri[q] = ti;
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < m) C.perm[b + k] = ri[k];
     return;
   }
   uint32_t idx[kCellSortCap];
