@@ -410,9 +410,9 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)  # before the process group, so NCCL binds this rank's GPU
     if world > 1:
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     _build.build()
     dev = torch.device("cuda", local)
     # a real stream (not the legacy default stream) so that the library can capture
