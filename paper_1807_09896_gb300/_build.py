@@ -7,6 +7,7 @@ no torch extension machinery: the library is a plain C-ABI shared object.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -47,6 +48,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)
+    # several processes (ranks of one job, test workers) may call this at once: one
+    # builds, the others wait for it and find the library up to date
+    with open(os.path.join(OUT, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and up_to_date():
+            return LIB
+        return _build_locked(verbose, extra_flags)
+
+
+def _build_locked(verbose, extra_flags) -> str:
     cc = nvcc()
     srcs = _sources()
 
