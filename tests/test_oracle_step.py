@@ -288,3 +288,30 @@ def test_couette_walls_drag_nearby_fluid_along_their_own_velocity():
     # force: together f_z is unchanged
     np.testing.assert_allclose(f[2, 2], f[0, 2], rtol=1e-12)
     np.testing.assert_array_equal(f0, 0.0)
+
+
+def test_bounce_back_mirror_error_is_third_order_in_the_displacement():
+    """Fig. 4 / Eq. 17 at a planar wall, phi = tanh(z / (sqrt(2) eps)) sampled on the grid.
+    On the exact profile atanh(phi) is proportional to the distance and the reflected
+    point is the exact mirror, z_bb = -z_new.  Trilinear interpolation makes phi linear
+    inside the wall's grid cells, where atanh(c z) = c z (1 + (c z)^2 / 3 + ...): the two
+    distances of the crossing fraction carry relative errors of second order in their
+    size, so the mirror is off by a term of third order in the step's displacement,
+    the same on every grid.  Halving the start height and the velocity divides the
+    error by 8."""
+    for h in (0.05, 0.25):
+        w = inputs.channel(3.0, 3.0, 3.0, seed=0, h=h)
+        f = _field(w)
+        p = oracle.Params(box=w.box, a_ff=0.0, gamma=0.0, sigma=0.0, dt=0.01)
+        errs = []
+        for k in (1.0, 0.5, 0.25, 0.125):
+            r0 = np.array([1.13, 1.31, 0.0137 * k])
+            v0 = np.array([0.7, -1.1, -3.3 * k])
+            s1, refl = oracle.step(oracle.init_forces(_lone_particle(w, r0, v0), p), p, f,
+                                   return_reflected=True)
+            assert refl[0]
+            z_new = r0[2] + v0[2] * p.dt
+            errs.append(abs(s1.pos[0, 2] + z_new))
+        ratios = np.array(errs[:-1]) / np.array(errs[1:])
+        assert np.all((ratios > 7.5) & (ratios < 8.5)), (h, errs)
+        assert errs[0] < 1e-5  # displacement 0.033 r_c: the mirror is right to 3e-4 of it
