@@ -390,3 +390,20 @@ def test_newton3_steps_repeat_bitwise():
     for x, y in zip(runs[0][0], runs[1][0]):
         np.testing.assert_array_equal(x, y)
     np.testing.assert_array_equal(runs[0][1], runs[1][1])
+
+
+def test_a_cell_beyond_48_particles_returns_overflow_not_a_fault():
+    """The per-cell id order holds at most 48 particles per cell (eight times more than
+    rho = 3 ever puts there); a crowded cell is reported as DPD_EOVERFLOW."""
+    w = inputs.bulk(5.0, seed=3)
+    pos = w.pos4()
+    rng = np.random.default_rng(0)
+    pos[:60, :3] = 2.0 + rng.uniform(0.0, 1.0, size=(60, 3))  # 60 particles in one unit cell
+    s = make_system(w, params_for(w), load=False)
+    with pytest.raises(dpd.DPDError) as e:
+        s.set_particles(pos, w.vel4(), w.id, w.type)
+        s.step(1)
+    assert e.value.code == dpd.DPD_EOVERFLOW
+    s.set_particles(w.pos4(), w.vel4(), w.id, w.type)  # a valid state clears it
+    s.step(2)
+    s.close()
