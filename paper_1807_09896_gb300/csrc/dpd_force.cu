@@ -22,9 +22,12 @@
 namespace dpd {
 
 // Launch shapes (threads per block, pair-list slots per thread, minimum resident
-// blocks per SM, unroll of the pair loop).  Every shape sums the same pairs in
-// the same order, so all of them give bit-identical forces; dpd_autotune picks
-// the fastest on the device at hand.
+// blocks per SM, unroll of the pair loop) of two algorithms: the full shell (every
+// pair from both sides, binary32 sums in a fixed order) and Newton's third law
+// (every pair once, fixed-point sums; further below).  Within an algorithm every
+// shape sums the same pairs in the same order, so its shapes give bit-identical
+// forces; dpd_autotune picks the fastest on the device at hand.
+
 // Slope -dw/dv of the cubic spline of Eq. 23 (w = 1 - 3/2 v^2 + 3/4 v^3 below 1,
 // (2 - v)^3 / 4 below 2, 0 beyond).
 __device__ __forceinline__ float spline_slope(float v) {

@@ -156,10 +156,11 @@ __global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellLis
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of the per-cell counts, in three passes (block sums, scan of
-// the block sums, scan inside each block with the block offset).  No block
-// waits on another, so nothing can spin.  Warp scans use __shfl_up_sync.
-// The last pass also zeroes the counts for the next step.
+// Exclusive scan of the per-cell counts: block sums, then the scan inside each
+// block with the block's offset.  For up to kScanFuseMax blocks each block sums
+// the totals before it itself; beyond that a one-block pass scans the totals in
+// between.  No block waits on another, so nothing can spin.  Warp scans use
+// __shfl_up_sync.  The last pass also zeroes the counts for the next step.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 8;
