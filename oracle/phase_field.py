@@ -17,7 +17,7 @@ Without the curvature term (curvature=False) the right-hand side is that of Eq. 
 in every direction, and curved interfaces move (a sphere shrinks).
 
 The normal is undefined where grad phi = 0 (the centre of a blob, a saddle between
-two), and near such points its direction is ill-conditioned.  Reading: the second
+two), and near such points its direction is ill-conditioned.  Reading R15: the second
 derivative along the normal is blended into the Laplacian there,
 
     phi_nn = (n.H.n |grad phi|^2 + delta lap phi) / (|grad phi|^2 + delta),
