@@ -143,7 +143,8 @@ void engine_enqueue_sort(Engine& E) {
 }
 
 int engine_kernels_per_step(const Engine& E) {
-  return kKernelsPerStepBase + scan_kernels(E.ncells) + force_variant_kernels(E.force_variant);
+  const int rest = E.n > 0 ? kKernelsPerStepSort + force_variant_kernels(E.force_variant) : 0;
+  return integrate_kernels(E.n, E.nsys) + scan_kernels(E.ncells) + rest;
 }
 
 void engine_enqueue_force(Engine& E, int kick) {
@@ -155,7 +156,6 @@ void engine_enqueue_force(Engine& E, int kick) {
 static void enqueue_step_from(Engine& E, int c) {
   const Arrays& A = E.arr[c];
   const Arrays& B = E.arr[c ^ 1];
-  launch_bump_step(E.d_ctr, E.nsys, E.stream);
   launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
   launch_scan(E.cl, E.ncells, E.n, E.stream);
   launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
@@ -219,7 +219,6 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
     const Arrays& A = E.arr[E.cur];
     const Arrays& B = E.arr[E.cur ^ 1];
     cudaEventRecord(ev[0], E.stream);
-    launch_bump_step(E.d_ctr, E.nsys, E.stream);
     launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
     cudaEventRecord(ev[1], E.stream);
     launch_scan(E.cl, E.ncells, E.n, E.stream);

@@ -13,11 +13,10 @@
 
 namespace dpd {
 
-// Kernels one time step enqueues: counter bump, drift/reflect/key, three scan
-// passes, scatter, per-cell sort, gather, force.
-// Kernels of one step besides the scan and the force: bump, integrate, scatter, cell
-// sort, gather.
-constexpr int kKernelsPerStepBase = 5;
+// Kernels of the reorder in one step: scatter, per-cell sort, gather.  A step also
+// enqueues the drift (which advances the noise counter too), the scan passes and the
+// force.
+constexpr int kKernelsPerStepSort = 3;
 
 struct Engine {
   int nsys = 0, n = 0, ncells = 0;

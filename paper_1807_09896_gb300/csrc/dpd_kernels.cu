@@ -133,8 +133,11 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
 template <bool kBatch>
 __global__ void __launch_bounds__(256, kBatch ? 6 : 8) k_integrate(StepParams P0, const SysDesc* __restrict__ S,
                                                    int nsys, Arrays A, CellList C, int n,
-                                                   DevCounters* ctrs) {
+                                                   DevCounters* ctrs, int bump) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // Thread k < nsys advances system k's noise counter for the force of this step;
+  // nothing in this launch reads it (the host folds the bump in only when nsys <= n).
+  if (bump && i < nsys) ctrs[i].step += 1u;
   if (i >= n) return;
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
@@ -518,13 +521,19 @@ __global__ void k_bump_step(DevCounters* ctr, int nsys) {
 // ---------------------------------------------------------------------------
 static inline int blocks(long n, int t) { return (int)((n + t - 1) / t); }
 
+static bool bump_folded(int n, int nsys) { return n > 0 && nsys <= n; }
+
+int integrate_kernels(int n, int nsys) { return (n > 0 ? 1 : 0) + (bump_folded(n, nsys) ? 0 : 1); }
+
 void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
                       const CellList& C, int n, DevCounters* ctr, cudaStream_t s) {
+  const int bump = bump_folded(n, nsys) ? 1 : 0;
+  if (!bump) k_bump_step<<<blocks(nsys, 128), 128, 0, s>>>(ctr, nsys);
   if (n <= 0) return;
   if (nsys == 1)
-    k_integrate<false><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr);
+    k_integrate<false><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr, bump);
   else
-    k_integrate<true><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr);
+    k_integrate<true><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr, bump);
 }
 
 void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
@@ -581,8 +590,5 @@ void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, flo
     k_unsort<<<blocks(n, 256), 256, 0, s>>>(A, n, out_pos, out_vel, out_frc, out_id, out_type);
 }
 
-void launch_bump_step(DevCounters* ctr, int nsys, cudaStream_t s) {
-  k_bump_step<<<blocks(nsys, 128), 128, 0, s>>>(ctr, nsys);
-}
 
 }  // namespace dpd

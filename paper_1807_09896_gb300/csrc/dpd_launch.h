@@ -5,11 +5,15 @@
 
 namespace dpd {
 
+// Drift, reflection and cell key of every particle, after advancing each system's
+// noise counter (inside the drift launch when nsys <= n, else by a launch of its own).
 // P0: parameters of system 0, used directly when nsys == 1.
 void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
                       const CellList& C, int n, DevCounters* ctr, cudaStream_t s);
 void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
                 cudaStream_t s);
+// Kernels one launch_integrate enqueues.
+int integrate_kernels(int n, int nsys);
 int scan_blocks(int ncells);
 // Kernels one launch_scan enqueues (2 for up to 1024 scan blocks, else 3).
 int scan_kernels(int ncells);
@@ -32,7 +36,6 @@ void launch_load(const StepParams& P, const float4* in_pos, const float4* in_vel
                  cudaStream_t s);
 void launch_unsort(const Arrays& A, int n, float4* out_pos, float4* out_vel, float4* out_frc,
                    int* out_id, uint8_t* out_type, cudaStream_t s);
-void launch_bump_step(DevCounters* ctr, int nsys, cudaStream_t s);
 void set_global_error(const char* msg);
 
 }  // namespace dpd
