@@ -15,7 +15,8 @@
  *      phi < 0, at the sharp phi = 0 surface located with the interpolated
  *      phase field (Sec. II.C, Eq. 17, Fig. 4);
  *   3. a cell-list rebuild (counting sort of the particles by cell of edge
- *      >= r_c; cells hold their particles in ascending id order);
+ *      >= r_c; each cell holds its particles in the order they had in the
+ *      previous step's arrays, which start in id order);
  *   4. the pair force f_i = sum_j f_ij over all j within r_c = 1
  *      (Eq. 2), f_ij = f^C + f^D + f^R of Eqs. 3-10 with the random force
  *      sigma w_R xi_ij / sqrt(dt), xi_ij drawn from Philox4x32-10 keyed by the
@@ -125,7 +126,7 @@ int dpd_step(dpd_t* h, int nsteps);
 enum {
   DPD_PHASE_INTEGRATE = 0, /* counter bump + drift, reflection, cell key and count */
   DPD_PHASE_SCAN = 1,      /* exclusive scan of the cell counts */
-  DPD_PHASE_SORT = 2,      /* scatter, per-cell id order, gather into cell order */
+  DPD_PHASE_SORT = 2,      /* scatter, per-cell order, gather into cell order */
   DPD_PHASE_FORCE = 3,     /* pair force (Eqs. 3-10) + closing half-kick */
   DPD_NPHASES = 4
 };

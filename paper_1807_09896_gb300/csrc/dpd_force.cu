@@ -15,7 +15,8 @@
 // Every pair is evaluated from both sides (no atomics, no scatter): the noise key
 // is symmetric and the minimum-image separation is exactly antisymmetric, so
 // f_ji = -f_ij bit for bit.  The sum runs in a fixed order (cells in index
-// order, particles by id), which makes the result independent of scheduling.
+// order, each cell in the fixed order the reorder gives it), which makes the
+// result independent of scheduling.
 #include "dpd_common.cuh"
 #include "dpd_launch.h"
 

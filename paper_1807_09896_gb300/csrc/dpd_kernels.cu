@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* count, int
 }
 
 // ---------------------------------------------------------------------------
-// Counting-sort scatter, per-cell id order, and the gather that reorders the
+// Counting-sort scatter, per-cell order, and the gather that reorders the
 // particle arrays into cell order.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(CellList C, int n, DevCounters* ctr) {
@@ -273,13 +273,15 @@ __global__ void k_scatter(CellList C, int n, DevCounters* ctr) {
     atomicOr(&ctr->status, ST_OVERFLOW);  // inconsistent counts: never write out of range
 }
 
-// One thread per cell: put the cell's entries of perm in ascending particle id
-// order (insertion sort; cells hold a handful of particles, and up to 8 are sorted in
-// registers, the rest through a local array).  This makes the
-// order of every later floating-point sum independent of atomic timing.
+// One thread per cell: put the cell's entries of perm in ascending order (insertion
+// sort; cells hold a handful of particles, and up to 8 are sorted in registers, the
+// rest through a local array).  perm holds each particle's index in the previous cell
+// order, itself fixed (particles are loaded in id order), so every cell ends up in an
+// order that does not depend on atomic timing, and so does every later floating-point
+// sum.  Sorting the indices themselves needs no other load.
 constexpr int kCellSortCap = 48;
 
-__global__ void k_cell_sort(CellList C, const float4* pos, int n, int ncells, DevCounters* ctr) {
+__global__ void k_cell_sort(CellList C, int ncells, DevCounters* ctr) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
   const uint32_t b = C.start[c], e = C.start[c + 1];
@@ -291,24 +293,17 @@ __global__ void k_cell_sort(CellList C, const float4* pos, int n, int ncells, De
   }
   if (m <= 8) {
     // small cell (nearly all): sort in registers, fully unrolled
-    uint32_t ri[8], rk[8];
+    uint32_t ri[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      ri[k] = 0u;
-      rk[k] = 0xFFFFFFFFu;
-      if (k < m) {
-        ri[k] = min(C.perm[b + k], (uint32_t)(n - 1));
-        rk[k] = id_of(pos[ri[k]].w);
-      }
-    }
+    for (int k = 0; k < 8; ++k) ri[k] = k < m ? C.perm[b + k] : 0xFFFFFFFFu;
 #pragma unroll
     for (int a = 1; a < 8; ++a)
 #pragma unroll
       for (int q = a; q > 0; --q)
-        if (rk[q - 1] > rk[q]) {
-          const uint32_t tk = rk[q - 1], ti = ri[q - 1];
-          rk[q - 1] = rk[q]; ri[q - 1] = ri[q];
-          rk[q] = tk; ri[q] = ti;
+        if (ri[q - 1] > ri[q]) {
+          const uint32_t t = ri[q - 1];
+          ri[q - 1] = ri[q];
+          ri[q] = t;
         }
 #pragma unroll
     for (int k = 0; k < 8; ++k)
@@ -316,17 +311,13 @@ __global__ void k_cell_sort(CellList C, const float4* pos, int n, int ncells, De
     return;
   }
   uint32_t idx[kCellSortCap];
-  uint32_t key[kCellSortCap];
   for (int k = 0; k < m; ++k) {
-    const uint32_t j = min(C.perm[b + k], (uint32_t)(n - 1));
-    const uint32_t id = id_of(pos[j].w);
+    const uint32_t j = C.perm[b + k];
     int q = k;
-    while (q > 0 && key[q - 1] > id) {
-      key[q] = key[q - 1];
+    while (q > 0 && idx[q - 1] > j) {
       idx[q] = idx[q - 1];
       --q;
     }
-    key[q] = id;
     idx[q] = j;
   }
   for (int k = 0; k < m; ++k) C.perm[b + k] = idx[k];
@@ -482,10 +473,12 @@ __global__ void k_load(StepParams P, const float4* in_pos, const float4* in_vel,
     v = make_float4(vw.x, vw.y, vw.z, 0.0f);
   }
   if (!solid && phi_at(P, p.x, p.y, p.z) < 0.0f) atomicOr(&ctr->status, ST_LOST);
-  A.pos[i] = p;
-  A.vel[i] = solid ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
-  A.vt[i] = v;
-  A.frc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // stored at index id: the first cell order, and every later one, then does not
+  // depend on the order of the input
+  A.pos[id] = p;
+  A.vel[id] = solid ? make_float4(0.f, 0.f, 0.f, 0.f) : v;
+  A.vt[id] = v;
+  A.frc[id] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Unsort into id order (outputs may be null).
@@ -560,7 +553,7 @@ void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n,
                  DevCounters* ctr, cudaStream_t s) {
   if (n <= 0) return;
   k_scatter<<<blocks(n, 256), 256, 0, s>>>(C, n, ctr);
-  k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, src.pos, n, ncells, ctr);
+  k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, ncells, ctr);
   k_gather<<<blocks(n, 256), 256, 0, s>>>(src, dst, C.perm, n);
 }
 
