@@ -69,18 +69,18 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
   }
 }
 
-// Store the new pair force of target i and apply the closing half-kick
-// v(t+dt) = v(t) + dt/2 (F(t) + F(t+dt)), F = f + g (not for reflected particles).
+// Store the new pair force of target i and complete the closing kick
+// v(t+dt) = v(t) + dt/2 (F(t) + F(t+dt)), F = f + g: the drift kernel left
+// v(t) + dt/2 F(t) in vel, this adds dt/2 F(t+dt) (not for reflected particles).
 __device__ __forceinline__ void finish_target(const StepParams& P, const Arrays& A, int i, float4 vti,
                                               float fx, float fy, float fz, DevCounters* ctr,
                                               int kick) {
-  const float4 f_old = A.frc[i];
   A.frc[i] = make_float4(fx, fy, fz, 0.0f);
   if (kick && vti.w == 0.0f) {
     float4 v = A.vel[i];
-    v.x = fmaf(P.half_dt, (f_old.x + fx) + 2.0f * P.g[0], v.x);
-    v.y = fmaf(P.half_dt, (f_old.y + fy) + 2.0f * P.g[1], v.y);
-    v.z = fmaf(P.half_dt, (f_old.z + fz) + 2.0f * P.g[2], v.z);
+    v.x = fmaf(P.half_dt, fx + P.g[0], v.x);
+    v.y = fmaf(P.half_dt, fy + P.g[1], v.y);
+    v.z = fmaf(P.half_dt, fz + P.g[2], v.z);
     A.vel[i] = v;
   }
   if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&ctr->status, ST_NAN);
@@ -383,7 +383,10 @@ __global__ void __launch_bounds__(256) k_force_finish(StepParams P0, const SysDe
                                                       DevCounters* ctrs, int kick) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (is_solid(A.pos[i].w)) return;  // nothing accumulates for solid particles
+  if (is_solid(A.pos[i].w)) {  // nothing accumulates for solid particles
+    A.frc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   unsigned long long* ax = facc + i;
   unsigned long long* ay = ax + n;
   unsigned long long* az = ay + n;
@@ -415,7 +418,10 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
   if (i >= n) return;
   const float4 pi = A.pos[i];
-  if (is_solid(pi.w)) return;
+  if (is_solid(pi.w)) {  // solid particles feel no force (the reorder does not carry it)
+    A.frc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
     force_body<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,

@@ -56,6 +56,10 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
     float x = two_sum(p.x, dx, &lx), y = two_sum(p.y, dy, &ly), z = two_sum(p.z, dz, &lz);
     float4 vt = make_float4(fmaf(P.lam_dt, Fx, v.x), fmaf(P.lam_dt, Fy, v.y),
                             fmaf(P.lam_dt, Fz, v.z), 0.0f);
+    // first half of the closing kick, v + dt/2 F(t): the force kernel adds dt/2 F(t+dt),
+    // so F(t) is not needed after this kernel (the reorder does not carry it)
+    float4 vh = make_float4(fmaf(P.half_dt, Fx, v.x), fmaf(P.half_dt, Fy, v.y),
+                            fmaf(P.half_dt, Fz, v.z), 0.0f);
     if (fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) > P.margin) atomicOr(&ctr->status, ST_BAND);
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(&ctr->status, ST_NAN);
     if (P.band != nullptr && P.band[cell_of(P, p.x, p.y, p.z)]) {
@@ -86,7 +90,7 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
         }
         x = bx; y = by; z = bz;
         const float4 vb = make_float4(2.0f * vw.x - v.x, 2.0f * vw.y - v.y, 2.0f * vw.z - v.z, 0.0f);
-        A.vel[i] = vb;
+        vh = vb;  // a reflected particle keeps its new velocity (no kick)
         vt = make_float4(vb.x, vb.y, vb.z, 1.0f);
         atomicAdd(&ctr->reflections, 1ull);
       }
@@ -95,6 +99,7 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
     p.y = wrap_coord(y, P.L[1]);
     p.z = wrap_coord(z, P.L[2]);
     A.pos[i] = p;
+    A.vel[i] = vh;
     A.vt[i] = vt;
   } else if (P.moving) {
     // frozen particles are part of the solid, which moves with the wall velocity at
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(256) k_gather(Arrays src, Arrays dst, const ui
   dst.pos[d] = src.pos[s];
   dst.vt[d] = src.vt[s];
   dst.vel[d] = src.vel[s];
-  dst.frc[d] = src.frc[s];
+  // the force is not carried: the drift has used it, and the force kernel rewrites it
 }
 
 // ---------------------------------------------------------------------------
