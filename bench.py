@@ -46,9 +46,9 @@ PHASE_FIELD_BYTES_PER_NODE = 8
 # At rho = 3 with unit cells there are 81 candidates and 4/3 pi rho = 12.57 pairs.
 OPS_PER_CANDIDATE = 13
 OPS_PER_PAIR = 115
-# Algorithmic HBM bytes per particle and step of the whole step: integrate 88,
-# scan 5, scatter 12, per-cell order 13, gather 132, force 96 (design notes).
-BYTES_PER_PARTICLE_STEP = 346
+# Algorithmic HBM bytes per particle and step of the whole step: integrate 104,
+# scan 5, scatter 12, per-cell order 9, gather 100, force 80 (design notes).
+BYTES_PER_PARTICLE_STEP = 310
 SM_COUNT_GB300 = 152
 LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
