@@ -75,9 +75,11 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
 __device__ __forceinline__ void finish_target(const StepParams& P, const Arrays& A, int i, float4 vti,
                                               float fx, float fy, float fz, DevCounters* ctr,
                                               int kick) {
+  const bool kicked = kick && vti.w == 0.0f;
+  float4 v;
+  if (kicked) v = A.vel[i];  // before the store below: the arrays could alias
   A.frc[i] = make_float4(fx, fy, fz, 0.0f);
-  if (kick && vti.w == 0.0f) {
-    float4 v = A.vel[i];
+  if (kicked) {
     v.x = fmaf(P.half_dt, fx + P.g[0], v.x);
     v.y = fmaf(P.half_dt, fy + P.g[1], v.y);
     v.z = fmaf(P.half_dt, fz + P.g[2], v.z);
@@ -97,6 +99,9 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   const uint32_t step = ctr->step;
   const float4* __restrict__ pos = A.pos;
   const float4* __restrict__ vt = A.vt;
+  // the closing kick reads this particle's velocity after the whole pair loop: start
+  // bringing it into L2 now, so that the thread does not end on a DRAM round trip
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(A.vel + i));
 
   float fx = 0.f, fy = 0.f, fz = 0.f;
   int cnt = 0;
