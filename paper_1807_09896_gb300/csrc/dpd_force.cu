@@ -473,6 +473,11 @@ static const ForceVariant kForceVariants[] = {
     DPD_FORCE_VARIANT_N3(128, 12, 1, 1), DPD_FORCE_VARIANT_N3(128, 8, 1, 1),
     DPD_FORCE_VARIANT_N3(64, 12, 1, 1), DPD_FORCE_VARIANT_N3(256, 8, 1, 1),
     DPD_FORCE_VARIANT_N3(128, 16, 1, 1),
+    // capped at 64 registers or fewer: eight 128-thread (sixteen 64-thread) blocks per SM
+    DPD_FORCE_VARIANT_N3(128, 16, 8, 1), DPD_FORCE_VARIANT_N3(128, 12, 8, 1),
+    DPD_FORCE_VARIANT_N3(64, 16, 14, 1), DPD_FORCE_VARIANT_N3(128, 24, 8, 1),
+    DPD_FORCE_VARIANT_N3(64, 16, 16, 1), DPD_FORCE_VARIANT_N3(64, 24, 16, 1),
+    DPD_FORCE_VARIANT_N3(64, 12, 16, 1),
 };
 
 int force_variants() { return (int)(sizeof(kForceVariants) / sizeof(kForceVariants[0])); }
@@ -480,7 +485,10 @@ int force_variants() { return (int)(sizeof(kForceVariants) / sizeof(kForceVarian
 const char* force_variant_name(int v) {
   static const char* names[] = {"128x24", "128x16", "256x16", "64x24", "128x16/min12",
                                 "256x12/min6", "128x32", "128x24/unroll2", "128x16/min12/unroll2",
-                                "n3 128x12", "n3 128x8", "n3 64x12", "n3 256x8", "n3 128x16"};
+                                "n3 128x12", "n3 128x8", "n3 64x12", "n3 256x8", "n3 128x16",
+                                "n3 128x16/min8", "n3 128x12/min8", "n3 64x16/min14",
+                                "n3 128x24/min8", "n3 64x16/min16", "n3 64x24/min16",
+                                "n3 64x12/min16"};
   return (v >= 0 && v < force_variants()) ? names[v] : "?";
 }
 
