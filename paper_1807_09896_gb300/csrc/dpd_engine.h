@@ -49,7 +49,8 @@ void engine_free_graphs(Engine& E);
 void engine_free(Engine& E);
 // Cell build of the state in arr[cur] into arr[cur ^ 1] (set-up, nothing moves).
 void engine_enqueue_sort(Engine& E);
-// Pair force on arr[cur]; kick = 1 adds the closing half-kick.
+// Pair force on arr[cur]; kick = 1 adds dt/2 F(t+dt), completing the closing kick whose
+// first half the drift kernel stored in vel.
 void engine_enqueue_force(Engine& E, int kick);
 // One full time step from arr[cur]; flips cur.
 void engine_enqueue_step(Engine& E);

@@ -1,6 +1,6 @@
 // dpd_force.cu -- the pair-force kernel of the DPD step (Eqs. 2-10 of Xu &
-// Meakin, arXiv:1807.09896) fused with the closing half-kick of the modified
-// velocity-Verlet scheme.
+// Meakin, arXiv:1807.09896) fused with the second half of the closing kick of the
+// modified velocity-Verlet scheme (the drift kernel applies the first half).
 //
 // One thread per particle in cell order.  Each fluid particle i scans the 27
 // cells around its own (the three x-neighbour cells of a row are one
@@ -212,7 +212,7 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
 // result does not depend on the order in which the atomics land and stays bitwise
 // reproducible.  Solid particles take part as the first particle of a pair (their
 // pairs with fluid particles in their half shell) but receive nothing.  A second
-// pass converts the sums, applies the closing half-kick and clears them.
+// pass converts the sums, completes the closing kick and clears them.
 // ---------------------------------------------------------------------------
 constexpr float kFixScale = 4294967296.0f;  // 2^32
 constexpr float kFixInvF = 1.0f / 4294967296.0f;  // 2^-32
@@ -380,7 +380,7 @@ k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
 }
 
 // Second pass: the fixed-point sum becomes the force (one rounding from the exact
-// integer), the closing half-kick is applied and the sum cleared for the next step.
+// integer), the closing kick is completed and the sum cleared for the next step.
 template <bool kBatch>
 __global__ void __launch_bounds__(256) k_force_finish(StepParams P0, const SysDesc* __restrict__ S,
                                                       int nsys, Arrays A,

@@ -13,11 +13,13 @@ namespace dpd {
 // Step kernel 1: drift, predicted velocity, reflection, cell key.
 //
 // Groot-Warren modified velocity-Verlet (Sec. II.A, ref. 35), F = f + g:
-//   dr = dt v + dt^2/2 F,  r' = r + dr,  vt = v + lambda dt F.
+//   dr = dt v + dt^2/2 F,  r' = r + dr,  vt = v + lambda dt F,
+// and vel <- v + dt/2 F, the first half of the closing kick (the force kernel adds
+// dt/2 F(t+dt)), so the old force is not needed after this kernel.
 // Bounce-back (Sec. II.C, Eq. 17, Fig. 4): if phi(r') < 0 the particle is put
 // at r' - 2 s dr with s = atanh(-phi(r')) / (atanh(-phi(r')) + atanh(phi(r))),
 // its velocity becomes 2 v_wall - v(t) (also used as vt), and it is flagged so
-// that the closing half-kick is skipped.  If the reflected point still has
+// that the closing kick is skipped.  If the reflected point still has
 // phi < 0 the particle stays at r(t).  The test runs only for particles whose
 // starting cell is flagged in the band mask (Sec. II.C: bulk particles far from
 // phi = 0 need no test); the band is conservative for drifts up to `margin`,
