@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -120,7 +121,10 @@ class ClockSampler:
 
     def __init__(self, device_uuid=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to DPD_CLOCKS_DIR if set, else the temporary directory; the
+        # JSON line carries their summary
+        out_dir = os.environ.get("DPD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
         self.uuid = device_uuid
 
     def start(self):

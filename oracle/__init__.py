@@ -225,7 +225,7 @@ def forces(pos, vt, ids, types, p: Params, step: int, method: int = 1) -> np.nda
 
 def forces_sel(pos, vt, ids, types, p: Params, step: int, sel, method: int = 1):
     """Pair force (Eq. 2) on the particles listed in `sel` only, and for each of
-    them sum_j |f_ij| (the scale a force error is judged against)."""
+    them sum_j |f_ij| (the scale a force error is measured against)."""
     pos = _c(pos, np.float64)
     sel = _c(sel, np.int32)
     f = np.zeros((len(sel), 3), np.float64)

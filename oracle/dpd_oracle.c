@@ -397,7 +397,7 @@ int or_forces(int n, const double* pos, const double* vt, const int* id, const u
 
 /* As or_forces, for the particles listed in sel (nsel of them; nsel < 0 means
  * all) -- f and fabs_sum are indexed like sel.  fabs_sum (may be NULL)
- * receives sum_j |f_ij|, the scale against which a force error is judged. */
+ * receives sum_j |f_ij|, the scale against which a force error is measured. */
 int or_forces_sel(int n, const double* pos, const double* vt, const int* id,
                   const uint8_t* type, const double* P, uint32_t step, uint32_t sys,
                   uint64_t seed, int method, int nsel, const int* sel, double* f, double* fabs_sum) {

@@ -177,7 +177,7 @@ def compare_one_step(s, w, p, field, label=""):
         ds = min_image(pos1[~fluid].astype(np.float64) - pos0[~fluid] - p.dt * vwall[~fluid], w.box)
         assert np.abs(ds).max() < 4 * ulp32(max(w.box))
 
-    # forces at t+dt, judged at the GPU's own (binary32) new positions: the oracle's
+    # forces at t+dt, evaluated at the GPU's own (binary32) new positions: the oracle's
     # new positions are not rounded to binary32, and the force is steep enough in r
     # that this rounding alone would exceed the force tolerance
     vt = st0.vel + p.lam * p.dt * F0
