@@ -50,9 +50,28 @@ OPS_PER_PAIR = 115
 # Algorithmic HBM bytes per particle and step of the whole step: integrate 104,
 # scan 5, scatter 12, per-cell order 9, gather 100, force 80 (design notes).
 BYTES_PER_PARTICLE_STEP = 310
+# Algorithmic bytes of each phase's kernel(s), per fluid particle, per solid
+# particle and per cell (minimal traffic: every array the kernel must read or write,
+# once).  integrate: pos, vel, frc in; pos, vel, vt, key, rank out (a resting solid
+# particle: pos in, key and rank out).  scan: count read twice, start written, count
+# cleared.  scatter: key, rank, start in; perm out.  cell_sort: perm in and out,
+# start in.  gather: perm, then pos, vt, vel in and out.  force_pairs: full shell
+# pos, vt, vel in, frc and vel out; half shell pos, vt in and 24 B of fixed-point
+# sums.  force_finish: sums in and cleared, pos, vt, vel in, frc and vel out.
+PHASE_BYTES = {
+    "integrate": (104, 24, 0),
+    "scan": (0, 0, 16),
+    "scatter": (12, 12, 4),
+    "cell_sort": (8, 8, 8),
+    "gather": (100, 100, 0),
+    "force_pairs": {False: (80, 16, 0), True: (56, 32, 0)},
+    "force_finish": (128, 16, 0),
+}
 SM_COUNT_GB300 = 152
 LANES_PER_SM = 128
 FALLBACK_HBM_GBS = 6800.0
+GRAPH_STEPS = 20
+E2E_REPEATS = 3
 
 
 def _args():
@@ -61,13 +80,18 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="channel_1m", choices=["channel_1m", "channel_200k"])
+    ap.add_argument("--workload", default="channel_1m",
+                    choices=["channel_1m", "channel_200k", "spheres_c3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint and precision lines")
     ap.add_argument("--force-variant", type=int, default=-1,
                     help="use this pair-force launch shape instead of tuning (e.g. to profile it)")
     ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the extra workload lines (channel_200k, spheres_c3)")
+    ap.add_argument("--timed-ms", type=float, default=1500.0,
+                    help="repeat the K-step replay until about this much device time is timed")
     return ap.parse_args()
 
 
@@ -75,6 +99,11 @@ WORKLOADS = {
     # name: (Lx, Ly, gap H, g_x)
     "channel_1m": (80.0, 64.0, 64.0, 0.01),
     "channel_200k": (64.0, 32.0, 32.0, 0.01),
+}
+# complex geometry: periodic cube of edge L with nspheres non-overlapping solid
+# spheres of radius U(rmin, rmax), fluid in the pores, body force g_x
+SPHERE_WORKLOADS = {
+    "spheres_c3": (100.0, 40, 6.0, 12.0, 0.005),
 }
 
 
@@ -96,8 +125,77 @@ def reduce_over_ranks(ms: float, units: float, device=None):
 def _workload(name, seed):
     from paper_1807_09896_gb300 import inputs
 
+    if name in SPHERE_WORKLOADS:
+        L, nsph, rmin, rmax, gx = SPHERE_WORKLOADS[name]
+        return inputs.sphere_pack(L, nsph, rmin, rmax, seed=seed), gx
     Lx, Ly, H, gx = WORKLOADS[name]
     return inputs.channel(Lx, Ly, H, seed=seed), gx
+
+
+def _describe(name, w, gx):
+    if name in SPHERE_WORKLOADS:
+        L, nsph, rmin, rmax, _ = SPHERE_WORKLOADS[name]
+        return (f"{name}: periodic cube {L:g}^3 r_c, {nsph} solid spheres of radius U({rmin:g}, "
+                f"{rmax:g}), rho 3, a 25, gamma 4.5, sigma 3, kBT 1, dt 0.01, g_x {gx}")
+    return (f"{name}: plane Poiseuille channel, box {w.box[0]:g}x{w.box[1]:g}x{w.box[2]:g} r_c, "
+            f"gap {w.gap:g}, rho 3, a 25, gamma 4.5, sigma 3, kBT 1, dt 0.01, g_x {gx}")
+
+
+def prepare_graphs(s, graph_steps):
+    """Capture the step graphs of both buffer parities before any timing (a graph
+    of an even number of steps starts and ends in the same buffers; one single
+    step between the two replays flips the parity).  Advances 2 (graph_steps + 1)
+    steps and leaves the state in the buffers it started in."""
+    for _ in range(2):
+        s.step(graph_steps)
+        s.step(1)
+
+
+def time_replays(s, steps, stream, torch, dev, target_ms, min_repeats=5, max_repeats=2000,
+                 barrier=lambda: None):
+    """Device time of `steps` steps replayed from the prebuilt graphs, as the median
+    over R repeats (CUDA events on the library's stream around each call), with R
+    sized so that about target_ms of device time is timed.  Returns (median ms, R,
+    list of ms)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    est = max(e0.elapsed_time(e1), 1e-3)
+    reps = int(min(max_repeats, max(min_repeats, math.ceil(target_ms / est))))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    for a, b in ev:
+        a.record(stream)
+        s.step(steps)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    times = [a.elapsed_time(b) for a, b in ev]
+    return statistics.median(times), reps, times
+
+
+def per_kernel_roofline(ph, newton3, n_fluid, n_solid, ncells, hbm_peak, hbm_src):
+    """HBM fraction of each phase's kernel(s): algorithmic bytes per launch over the
+    phase's mean CUDA-event time."""
+    out = {}
+    for name, ms in ph.items():
+        spec = PHASE_BYTES[name]
+        if isinstance(spec, dict):
+            spec = spec[newton3]
+        if ms <= 0.0 or (name == "force_finish" and not newton3):
+            continue
+        bpf, bps, bpc = spec
+        nbytes = bpf * n_fluid + bps * n_solid + bpc * ncells
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes_per_launch": nbytes, "achieved": gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": gbs / hbm_peak, "peak_source": hbm_src,
+                     "bound": "alu" if name == "force_pairs" else "hbm"}
+    return out
 
 
 def _peaks():
@@ -196,6 +294,8 @@ def cpu_oracle_rate(name, budget_s=10.0, min_steps=2, max_steps=None, warmup=0, 
     import oracle
     from paper_1807_09896_gb300 import inputs
 
+    if name in SPHERE_WORKLOADS:
+        return _cpu_oracle_rate_whole(name, budget_s, min_steps, max_steps, warmup, seed)
     Lx, Ly, H, gx = WORKLOADS[name]
     # calibrate on a small slice, then size the slice to the budget
     probe = inputs.channel(6.0, 6.0, H, seed=seed)
@@ -235,6 +335,35 @@ def cpu_oracle_rate(name, budget_s=10.0, min_steps=2, max_steps=None, warmup=0, 
                       f"steps in {el:.1f} s after {warmup} untimed"}
 
 
+def _cpu_oracle_rate_whole(name, budget_s, min_steps, max_steps, warmup, seed):
+    """FP64 oracle throughput on the whole workload (its steps take about a second)."""
+    import numpy as np
+
+    import oracle
+
+    w, gx = _workload(name, seed)
+    p = oracle.Params(box=w.box, g=(gx, 0, 0), seed=seed)
+    field = oracle.Field(w.phi, w.h)
+    st = oracle.State(w.pos.astype(np.float64), w.vel.astype(np.float64), np.zeros((w.n, 3)),
+                      w.id.copy(), w.type.copy())
+    st = oracle.init_forces(st, p)
+    for _ in range(warmup):
+        st = oracle.step(st, p, field)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        st = oracle.step(st, p, field)
+        done += 1
+        el = time.perf_counter() - t0
+        if max_steps and done >= max_steps:
+            break
+        if not max_steps and done >= min_steps and el >= budget_s:
+            break
+    return {"value": w.n_fluid * done / el, "unit": "particle-steps/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the whole {name} workload ({w.n_fluid} fluid + {w.n_solid} solid "
+                      f"particles), {done} FP64 steps in {el:.1f} s after {warmup} untimed"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -260,6 +389,40 @@ def run_reference(args):
     }
     print(json.dumps(line))
     return 0
+
+
+def measure_workload(dpd, torch, dev, stream, rank, name, steps, timed_ms, hbm_peak, hbm_src,
+                     barrier):
+    """Throughput line of another workload, measured like the headline one: tuned
+    force shape, graphs captured first, median over repeats of a K-step replay."""
+    t0 = time.perf_counter()
+    w, gx = _workload(name, seed=rank)
+    gen_s = time.perf_counter() - t0
+    s = dpd.System.from_workload(w, g=(gx, 0.0, 0.0))
+    dpd.dpd_set_stream(s.h, stream)
+    s.set_option("use_graph", 1)
+    s.set_option("graph_steps", GRAPH_STEPS)
+    s.set_option("seed", rank)
+    s.step(GRAPH_STEPS)
+    chosen, _ = dpd.dpd_autotune(s.h, 3)
+    newton3 = bool(s.get_option("force_newton3"))
+    prepare_graphs(s, GRAPH_STEPS)
+    ms, reps, _ = time_replays(s, steps, stream, torch, dev, timed_ms / 3, barrier=barrier)
+    ms, units = reduce_over_ranks(ms, float(w.n_fluid) * steps, device=dev)
+    ph = dpd.dpd_time_phases(s.h, min(steps, 20))
+    st = s.stats()
+    s.close()
+    ncells = int(w.box[0]) * int(w.box[1]) * int(w.box[2])
+    step_gbs = BYTES_PER_PARTICLE_STEP * (w.n_fluid + w.n_solid) * steps / (ms / 1e3) / 1e9
+    return {"workload": _describe(name, w, gx), "n_fluid": w.n_fluid, "n_solid": w.n_solid,
+            "value": units / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms / steps,
+            "steps": steps, "repeats": reps, "force_launch_shape": chosen,
+            "step_hbm": {"achieved": step_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": step_gbs / hbm_peak, "peak_source": hbm_src,
+                         "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
+            "per_kernel": per_kernel_roofline(ph, newton3, w.n_fluid, w.n_solid, ncells, hbm_peak,
+                                              hbm_src),
+            "reflections": st[5], "fallbacks": st[6], "input_generation_s": gen_s}
 
 
 def measure_batched(dpd, torch, dev, stream, rank, nsys=64, steps=200):
@@ -428,7 +591,7 @@ def run_ours(args):
     s = dpd.System.from_workload(w, g=(gx, 0.0, 0.0))
     dpd.dpd_set_stream(s.h, stream)
     s.set_option("use_graph", 1)
-    s.set_option("graph_steps", 20)
+    s.set_option("graph_steps", GRAPH_STEPS)
     s.set_option("seed", rank)
 
     def barrier():
@@ -443,9 +606,9 @@ def run_ours(args):
     else:
         chosen, _ = dpd.dpd_autotune(s.h, 5)
     newton3 = bool(s.get_option("force_newton3"))
-    s.step(2)
+    # the timed region replays graphs only: capture them first (tuning drops them)
+    prepare_graphs(s, GRAPH_STEPS)
     torch.cuda.synchronize(dev)
-    launches0 = s.get_option("kernel_launches")
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -454,25 +617,19 @@ def run_ours(args):
     clocks = ClockSampler(uuid)
     clocks.start()
     time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    ms = e0.elapsed_time(e1)
+    launches0 = s.get_option("kernel_launches")
+    ms, reps, rep_ms = time_replays(s, args.steps, stream, torch, dev, args.timed_ms,
+                                    barrier=barrier)
     ck = clocks.stop()
-    launches = int(s.get_option("kernel_launches") - launches0)
+    # kernels of one timed K-step call (every repeat launches the same ones)
+    launches = int(round((s.get_option("kernel_launches") - launches0) / (reps + 1)))
     ms, units = reduce_over_ranks(ms, float(w.n_fluid) * args.steps, device=dev)
     value = units / (ms / 1e3)
 
     # phase durations with CUDA events on the library's stream (same launches, no graph)
     nph = min(args.steps, 50)
     ph = dpd.dpd_time_phases(s.h, nph)
-    force_ms = ph["force"]
+    force_ms = ph["force_pairs"] + ph["force_finish"]
     # the unit of work is fixed per particle-step (27 cells of candidates, every pair in
     # r_c), whichever algorithm runs; the half shell's own count is reported beside it
     cand = 27 * 3.0                    # 27 cells of unit volume at rho = 3
@@ -487,6 +644,8 @@ def run_ours(args):
     traffic = (_force_traffic() or {}).get("variants", {}).get(str(chosen))
     hbm_peak, hbm_src, _ = _peaks()
     step_gbs = BYTES_PER_PARTICLE_STEP * (w.n_fluid + w.n_solid) * args.steps / (ms / 1e3) / 1e9
+    ncells = int(w.box[0]) * int(w.box[1]) * int(w.box[2])
+    kernels = per_kernel_roofline(ph, newton3, w.n_fluid, w.n_solid, ncells, hbm_peak, hbm_src)
 
     # end to end through the public API from pinned host buffers
     pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
@@ -497,16 +656,20 @@ def run_ours(args):
     oi, ot = pin((w.n,), torch.int32), pin((w.n,), torch.uint8)
     nb = 64
     prof = pin((nb, 5), torch.float64)
+    prof_hi = w.gap if w.gap else w.box[2]
+    e2e_times = []
+    for _ in range(E2E_REPEATS):
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s.set_particles(hp, hv, hi, ht)
+        s.step(args.steps)
+        dpd.dpd_velocity_profile(s.h, 2, nb, 0.0, prof_hi, mode=1, out=prof)
+        dpd.dpd_get_state(s.h, op, ov, of, oi, ot)
+        torch.cuda.synchronize(dev)
+        e2e_times.append(time.perf_counter() - t0)
     barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    s.set_particles(hp, hv, hi, ht)
-    s.step(args.steps)
-    dpd.dpd_velocity_profile(s.h, 2, nb, 0.0, w.gap, mode=1, out=prof)
-    dpd.dpd_get_state(s.h, op, ov, of, oi, ot)
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    barrier()
+    e2e_s = statistics.median(e2e_times)
     e2e_s, e2e_units = reduce_over_ranks(e2e_s, float(w.n_fluid) * args.steps, device=dev)
     e2e = e2e_units / e2e_s
     h2d = w.n * (16 + 16 + 4 + 1)
@@ -514,6 +677,12 @@ def run_ours(args):
     st = s.stats()
     s.close()
 
+    extra = {}
+    if not args.no_workloads:
+        for name in ("channel_200k", "spheres_c3"):
+            if name != args.workload:
+                extra[name] = measure_workload(dpd, torch, dev, stream, rank, name, args.steps,
+                                               args.timed_ms, hbm_peak, hbm_src, barrier)
     batched = None if args.no_batched else measure_batched(dpd, torch, dev, stream, rank,
                                                             steps=args.batched_steps)
     adj = None if args.no_extras else measure_adjoint(dpd, torch, dev, stream)
@@ -531,15 +700,15 @@ def run_ours(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": f"{args.workload}: plane Poiseuille channel, box "
-                            f"{w.box[0]:g}x{w.box[1]:g}x{w.box[2]:g} r_c, gap {w.gap:g}, rho 3, "
-                            f"a 25, gamma 4.5, sigma 3, kBT 1, dt 0.01, g_x {gx}",
+                "workload": _describe(args.workload, w, gx),
                 "n_fluid": w.n_fluid, "n_solid": w.n_solid,
                 "value_counts": "fluid particles only",
                 "l2": "inputs larger than L2: particle state 2 x %.0f MB + phase field %.0f MB" % (
                     w.n * 64 / 1e6, w.phi.nbytes / 1e6),
-                "graph_steps": 20, "parallelism": f"replicas x{world}",
+                "graph_steps": GRAPH_STEPS, "parallelism": f"replicas x{world}",
                 "force_launch_shape": chosen,
+                "timing": f"median over {reps} repeats of the K-step call (graphs captured before "
+                          f"timing; repeats {min(rep_ms):.4f}-{max(rep_ms):.4f} ms)",
             },
             "roofline": {
                 "kernel": ("k_force_n3 + k_force_finish (half-shell pair force, fixed-point sums, "
@@ -555,14 +724,17 @@ def run_ours(args):
                 "step_hbm": {"achieved": step_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": step_gbs / hbm_peak, "peak_source": hbm_src,
                              "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
+                "per_kernel": kernels,
             },
             "e2e": {"value": e2e, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "note": "pinned host state in, K steps, profile + state out, per call"},
+                    "note": f"pinned host state in, K steps, profile + state out, per call; median "
+                            f"of {E2E_REPEATS} calls"},
             "gpu_launches": launches,
             "clocks": ck,
             "cpu_baseline": cpu,
             "diagnostics": {"reflections": st[5], "fallbacks": st[6]},
+            "workloads": extra,
             "batched": batched,
             "adjoint": adj,
             "fp32_vs_fp64": precision,

@@ -122,13 +122,17 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
  * DPD_EOVERFLOW and stays set until the next dpd_set_particles. */
 int dpd_step(dpd_t* h, int nsteps);
 
-/* Phases of one time step, in launch order, as timed by dpd_time_phases. */
+/* Phases of one time step, in launch order, as timed by dpd_time_phases: one
+ * kernel each, except the scan (two or three launches). */
 enum {
   DPD_PHASE_INTEGRATE = 0, /* counter bump + drift, reflection, cell key and count */
   DPD_PHASE_SCAN = 1,      /* exclusive scan of the cell counts */
-  DPD_PHASE_SORT = 2,      /* scatter, per-cell order, gather into cell order */
-  DPD_PHASE_FORCE = 3,     /* pair force (Eqs. 3-10) + closing half-kick */
-  DPD_NPHASES = 4
+  DPD_PHASE_SCATTER = 2,   /* counting-sort scatter of the particle indices */
+  DPD_PHASE_CELL_SORT = 3, /* per-cell order (previous index, ascending) */
+  DPD_PHASE_GATHER = 4,    /* gather of the particle arrays into cell order */
+  DPD_PHASE_FORCE = 5,     /* pair force (Eqs. 3-10); full-shell shapes also finish the kick */
+  DPD_PHASE_FINISH = 6,    /* Newton's-third-law shapes: sums -> force, closing kick (else 0) */
+  DPD_NPHASES = 7
 };
 
 /* Advance nsteps > 0 time steps exactly as dpd_step does, but launched one by one
@@ -210,9 +214,14 @@ int dpd_relax_phase_field(float* phi, const int dims[3], double spacing, double 
  * 5 doubles (160 KiB) that every GPU loading the library keeps until the
  * process exits.  Every call shares it: each call clears what it uses first,
  * and calls whose work overlaps on the GPU (e.g. on two streams) race and give
- * wrong sums.  The first call on a device looks up that array's device address
- * (once per device, with the device current); make that first call before any
- * stream capture begins.  Errors: dpd_last_error(NULL) holds the message. */
+ * wrong sums.  The first call in a CUDA context (per device, and again after a
+ * cudaDeviceReset) looks up that array's device address with the device
+ * current; make that first call before any stream capture begins.  The array
+ * itself comes into being when the library's device code is loaded into the
+ * context: under CUDA's default lazy loading that can be inside the first call,
+ * so a process that will run under a hard memory cap should make one call
+ * (or set CUDA_MODULE_LOADING=EAGER) before the cap applies.
+ * Errors: dpd_last_error(NULL) holds the message. */
 int dpd_velocity_profile_noalloc(const float* pos4, const float* vel4, const uint8_t* type, int n,
                                  int axis, int nbins, double lo, double hi, double* out, int where,
                                  void* stream);
@@ -266,8 +275,10 @@ int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
  * again from its counter, drift, predicted velocity, closing kick, and Eq. 17
  * reflection including the gradient of the interpolated phase field).  Events
  * are frozen: reflection decisions, cell lists and bin membership are those of
- * the forward trajectory.  tie_sigma = 1 keeps sigma = sqrt(2 gamma kBT) (Eq. 8)
- * so d/dgamma includes the random force; 0 holds sigma fixed.  grad[3] receives
+ * the forward trajectory.  tie_sigma = 1 first sets sigma = sqrt(2 gamma kBT)
+ * (Eq. 8; the system keeps that sigma) and differentiates through the tie, so
+ * d/dgamma includes the random force (DPD_EINVAL unless kBT > 0 and gamma > 0);
+ * 0 runs with sigma as set and holds it fixed.  grad[3] receives
  * dL/da_fs, dL/dgamma, dL/dg_x; loss_out (may be NULL) receives L.
  * Memory: a checkpoint every ckpt_every steps (nsteps must be a multiple) and a
  * record of ckpt_every steps; the backward pass recomputes one segment at a

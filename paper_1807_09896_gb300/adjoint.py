@@ -11,7 +11,6 @@ and the adjoint at once; backward only scales the stored gradient.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -44,20 +43,19 @@ class NearWallLoss:
         return len(self.target)
 
 
-def set_theta(system, theta, tie_sigma=True):
-    """Write (a_fs, gamma, g_x) into a System; sigma follows gamma by Eq. 8 if tied."""
+def set_theta(system, theta):
+    """Write (a_fs, gamma, g_x) into a System.  With tie_sigma the library itself
+    sets sigma from gamma (Eq. 8) when the window starts."""
     a_fs, gamma, g_x = (float(x) for x in theta)
     system.set_option("a_fs", a_fs)
     system.set_option("gamma", gamma)
-    if tie_sigma:
-        system.set_option("sigma", math.sqrt(2.0 * gamma * system.get_option("kBT")))
     system.set_option("g_x", g_x)
 
 
 def window_loss_and_grad(system, theta, loss: NearWallLoss, nsteps: int, ckpt_every: int,
                          tie_sigma: bool = True):
     """Set theta, run the window on the GPU, return (L, dL/dtheta)."""
-    set_theta(system, theta, tie_sigma)
+    set_theta(system, theta)
     return dpd.dpd_adjoint_window(system.h, nsteps, ckpt_every, loss.axis, loss.wall_lo,
                                   loss.wall_hi, loss.target, loss.width, tie_sigma)
 

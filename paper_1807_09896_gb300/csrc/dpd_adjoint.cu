@@ -363,10 +363,13 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
   if (h->force_law != 0) return afail(h, DPD_EINVAL, "the adjoint supports force_law 0");
   if (h->shear[0] != 0.0 || h->shear[1] != 0.0 || h->shear[2] != 0.0)
     return afail(h, DPD_EINVAL, "the adjoint supports walls moving together (shear 0)");
-  if (tie_sigma && !(h->kBT > 0.0 && h->sigma > 0.0))
-    return afail(h, DPD_EINVAL, "tying sigma to gamma needs kBT > 0 and sigma > 0");
+  if (tie_sigma && !(h->kBT > 0.0 && h->gamma > 0.0))
+    return afail(h, DPD_EINVAL, "tying sigma to gamma needs kBT > 0 and gamma > 0");
   Engine& E = h->E;
   if (E.h_ctr[0].status) return engine_status_code(E, E.h_ctr[0].status);
+  // Eq. 8, sigma^2 = 2 gamma kBT: the forward window runs with the sigma that the
+  // gradient assumes (the system keeps it)
+  if (tie_sigma) h->sigma = std::sqrt(2.0 * h->gamma * h->kBT);
   h->params_dirty = true;
   {
     // parameters as set now

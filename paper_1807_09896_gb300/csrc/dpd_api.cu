@@ -221,7 +221,8 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
   if (n >= (1 << 30)) return fail(h, DPD_EOVERFLOW, "too many particles");
   dpd::Engine& E = h->E;
   h->loaded = false;
-  dpd::engine_free_graphs(E);
+  // captured graphs stay valid while the buffers, sizes and parameters do (engine_step
+  // compares them; engine_reserve drops the graphs when it reallocates)
   int rc = dpd::engine_reserve(E, 1, n, h->ncells);
   if (rc) return rc;
   if (n > h->out_cap) {
@@ -241,19 +242,34 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
   rc = sync_params(h);
   if (rc) return rc;
   int nf = 0;
-  // Stage the inputs on the device.
+  // Stage the inputs on the device (staging buffers grow only and are kept).
+  const bool host = where == DPD_HOST;
+  if (n > h->in_cap) {
+    cudaFree(h->d_in4);
+    cudaFree(h->d_in_id);
+    cudaFree(h->d_in_type);
+    cudaFree(h->d_seen);
+    h->d_in4 = nullptr;
+    h->d_in_id = nullptr;
+    h->d_in_type = nullptr;
+    h->d_seen = nullptr;
+    h->in_cap = 0;
+    CU(h, dev_alloc(&h->d_in4, (size_t)2 * n));
+    CU(h, dev_alloc(&h->d_in_id, n));
+    CU(h, dev_alloc(&h->d_in_type, n));
+    CU(h, dev_alloc(&h->d_seen, n));
+    h->in_cap = n;
+  }
   float4 *in_pos = nullptr, *in_vel = nullptr;
   int* in_id = nullptr;
   uint8_t* in_type = nullptr;
-  uint32_t* seen = nullptr;
+  uint32_t* seen = h->d_seen;
   std::vector<uint8_t> host_type;
-  const bool host = where == DPD_HOST;
-  CU(h, dev_alloc(&seen, n));
   if (host) {
-    CU(h, dev_alloc(&in_pos, n));
-    CU(h, dev_alloc(&in_vel, n));
-    CU(h, dev_alloc(&in_id, n));
-    CU(h, dev_alloc(&in_type, n));
+    in_pos = h->d_in4;
+    in_vel = h->d_in4 + n;
+    in_id = h->d_in_id;
+    in_type = h->d_in_type;
     CU(h, cudaMemcpyAsync(in_pos, pos4, sizeof(float4) * n, cudaMemcpyHostToDevice, E.stream));
     CU(h, cudaMemcpyAsync(in_vel, vel4, sizeof(float4) * n, cudaMemcpyHostToDevice, E.stream));
     CU(h, cudaMemcpyAsync(in_id, id, sizeof(int) * n, cudaMemcpyHostToDevice, E.stream));
@@ -277,15 +293,8 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
   dpd::engine_enqueue_force(E, 0);  // f(0) with vt = v(0)
   cudaError_t le = cudaGetLastError();
   cudaError_t se = cudaStreamSynchronize(E.stream);
-  cudaFree(seen);
-  if (host) {
-    cudaFree(in_pos);
-    cudaFree(in_vel);
-    cudaFree(in_id);
-    cudaFree(in_type);
-  } else {
+  if (!host)
     for (int i = 0; i < n; ++i) nf += host_type[i] == 0;
-  }
   if (le != cudaSuccess) return fail(h, DPD_ECUDA, "launch failed: %s", cudaGetErrorString(le));
   if (se != cudaSuccess) return fail(h, DPD_ECUDA, "set-up failed: %s", cudaGetErrorString(se));
   uint32_t st = 0;
@@ -596,6 +605,10 @@ int dpd_destroy(dpd_t* h) {
   cudaFree(h->d_out4);
   cudaFree(h->d_out_id);
   cudaFree(h->d_out_type);
+  cudaFree(h->d_in4);
+  cudaFree(h->d_in_id);
+  cudaFree(h->d_in_type);
+  cudaFree(h->d_seen);
   cudaFree(h->d_phi);
   cudaFree(h->d_band);
   cudaFree(h->d_prof);

@@ -33,6 +33,10 @@ struct Engine {
   // particle, zero between steps (the finish kernel clears what it reads)
   unsigned long long* facc = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // what the graphs were captured with (system 0's parameters travel by value in
+  // the kernel arguments; sizes set the grids): a replay with anything else rebuilds
+  StepParams graph_P = {};
+  int graph_n = -1, graph_ncells = -1, graph_nsys = -1, graph_variant = -1, graph_len = -1;
   int use_graph = 1, graph_steps = 20, force_variant = 0;
   uint64_t launches = 0;
   std::string* err = nullptr;  // where failure messages go

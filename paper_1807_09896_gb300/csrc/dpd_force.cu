@@ -497,9 +497,9 @@ int force_variant_kernels(int variant) {
   return kForceVariants[variant].n3 ? 2 : 1;
 }
 
-void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                  const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr, int kick,
-                  int variant, cudaStream_t s) {
+void launch_force_pairs(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                        const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr,
+                        int kick, int variant, cudaStream_t s) {
   if (n <= 0) return;
   if (variant < 0 || variant >= force_variants()) variant = 0;
   const ForceVariant& fv = kForceVariants[variant];
@@ -512,11 +512,26 @@ void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays
   }
   (nsys == 1 ? fv.single3[law] : fv.batch3[law])<<<nb, fv.threads, 0, s>>>(P0, S, nsys, A, start, facc,
                                                                             n, ctr);
+}
+
+void launch_force_finish(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                         unsigned long long* facc, int n, DevCounters* ctr, int kick, int variant,
+                         cudaStream_t s) {
+  if (n <= 0) return;
+  if (variant < 0 || variant >= force_variants()) variant = 0;
+  if (!kForceVariants[variant].n3) return;
   const int nb2 = (n + 255) / 256;
   if (nsys == 1)
     k_force_finish<false><<<nb2, 256, 0, s>>>(P0, S, nsys, A, facc, n, ctr, kick);
   else
     k_force_finish<true><<<nb2, 256, 0, s>>>(P0, S, nsys, A, facc, n, ctr, kick);
+}
+
+void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                  const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr, int kick,
+                  int variant, cudaStream_t s) {
+  launch_force_pairs(P0, S, nsys, A, start, facc, n, ctr, kick, variant, s);
+  launch_force_finish(P0, S, nsys, A, facc, n, ctr, kick, variant, s);
 }
 
 }  // namespace dpd

@@ -556,12 +556,23 @@ void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s) {
   }
 }
 
+void launch_scatter(const CellList& C, int n, DevCounters* ctr, cudaStream_t s) {
+  if (n > 0) k_scatter<<<blocks(n, 256), 256, 0, s>>>(C, n, ctr);
+}
+
+void launch_cell_sort(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s) {
+  if (n > 0) k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, ncells, ctr);
+}
+
+void launch_gather(const CellList& C, const Arrays& src, const Arrays& dst, int n, cudaStream_t s) {
+  if (n > 0) k_gather<<<blocks(n, 256), 256, 0, s>>>(src, dst, C.perm, n);
+}
+
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s) {
-  if (n <= 0) return;
-  k_scatter<<<blocks(n, 256), 256, 0, s>>>(C, n, ctr);
-  k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, ncells, ctr);
-  k_gather<<<blocks(n, 256), 256, 0, s>>>(src, dst, C.perm, n);
+  launch_scatter(C, n, ctr, s);
+  launch_cell_sort(C, n, ncells, ctr, s);
+  launch_gather(C, src, dst, n, s);
 }
 
 void launch_profile(const float4* pos, const float4* vel, int n, int axis, int nbins, float lo,

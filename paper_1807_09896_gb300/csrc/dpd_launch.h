@@ -18,11 +18,23 @@ int scan_blocks(int ncells);
 // Kernels one launch_scan enqueues (2 for up to 1024 scan blocks, else 3).
 int scan_kernels(int ncells);
 void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s);
+// Reorder into cell order: scatter, per-cell sort, gather (launch_sort = all three).
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s);
+void launch_scatter(const CellList& C, int n, DevCounters* ctr, cudaStream_t s);
+void launch_cell_sort(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s);
+void launch_gather(const CellList& C, const Arrays& src, const Arrays& dst, int n, cudaStream_t s);
+// Pair force of the given launch shape; launch_force = the pair kernel, then (for
+// the Newton's-third-law shapes) the finish pass.
 void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
                   const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr, int kick,
                   int variant, cudaStream_t s);
+void launch_force_pairs(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                        const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr,
+                        int kick, int variant, cudaStream_t s);
+void launch_force_finish(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                         unsigned long long* facc, int n, DevCounters* ctr, int kick, int variant,
+                         cudaStream_t s);
 int force_variants();
 // Kernels one launch_force of this shape enqueues (1, or 2 with the finish pass).
 int force_variant_kernels(int variant);

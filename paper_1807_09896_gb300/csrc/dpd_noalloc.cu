@@ -9,8 +9,11 @@
 // FP64 bin accumulators live in a fixed, file-scope device array that every GPU
 // loading the library holds until the process exits (kNoAllocMaxBins x 5
 // doubles = 160 KiB).
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "../../include/dpd.h"
 #include "dpd_common.cuh"
@@ -19,28 +22,70 @@
 namespace {
 
 constexpr int kNoAllocMaxBins = DPD_NOALLOC_MAX_BINS;
-constexpr int kMaxDevices = 64;
 
 // Accumulators shared by every call on a device.  Each call clears the part it
 // uses before accumulating; calls that overlap on the GPU (different streams)
 // race on this array.
 static __device__ __align__(256) double g_profile_scratch[5 * kNoAllocMaxBins];
 
+// Device address of g_profile_scratch in each CUDA context this process used,
+// keyed by the context's unique id: a context created after a cudaDeviceReset (or
+// any new context on the same device) reloads the module, so its array has a new
+// address, and a key by device ordinal alone would hand out a stale one.  In host
+// code the symbol itself is only a host-side stand-in; a kernel given it would
+// fault or touch the wrong memory, so only these addresses are passed.
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  void* addr;
+};
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+std::vector<ScratchEntry> g_scratch;
 
-// Device address of g_profile_scratch on the current device, looked up once per
-// device.  In host code the symbol itself is only a host-side stand-in; a kernel
-// given it would fault or touch the wrong memory, so only this address is passed.
-cudaError_t scratch_address(int dev, void** out) {
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+std::once_flag g_entry_once;
+
+// Driver entry points through the runtime (no link against the driver library).
+void find_entry_points() {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+          cudaSuccess && q == cudaDriverEntryPointSuccess)
+    g_ctx_current = (CtxGetCurrentFn)f;
+  f = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+          cudaSuccess && q == cudaDriverEntryPointSuccess)
+    g_ctx_id = (CtxGetIdFn)f;
+}
+
+// Address of the scratch array in the current context: looked up with
+// cudaGetSymbolAddress once per context (the runtime makes the device's primary
+// context current on that first lookup), then taken from the table.
+cudaError_t scratch_address(void** out) {
+  std::call_once(g_entry_once, find_entry_points);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_profile_scratch);
+  if (!g_ctx_current || !g_ctx_id) return cudaGetSymbolAddress(out, g_profile_scratch);
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) {
+    // no context yet on this thread: the lookup creates the primary one
+    const cudaError_t e = cudaGetSymbolAddress(out, g_profile_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return cudaSuccess;
   }
-  *out = g_scratch_addr[dev];
+  unsigned long long id = 0;
+  if (g_ctx_id(ctx, &id) != CUDA_SUCCESS) return cudaGetSymbolAddress(out, g_profile_scratch);
+  for (const ScratchEntry& en : g_scratch)
+    if (en.ctx_id == id) {
+      *out = en.addr;
+      return cudaSuccess;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_profile_scratch);
+  if (e != cudaSuccess) return e;
+  g_scratch.push_back({id, p});
+  *out = p;
   return cudaSuccess;
 }
 
@@ -121,10 +166,8 @@ extern "C" int dpd_velocity_profile_noalloc(const float* pos4, const float* vel4
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return nofail("dpd_velocity_profile_noalloc: no CUDA device", DPD_ECUDA);
-  if (dev < 0 || dev >= kMaxDevices)
-    return nofail("dpd_velocity_profile_noalloc: device ordinal %ld beyond %ld", DPD_EINVAL, dev, kMaxDevices);
   void* scratch = nullptr;
-  e = scratch_address(dev, &scratch);
+  e = scratch_address(&scratch);
   if (e != cudaSuccess)
     return nofail("dpd_velocity_profile_noalloc: cudaGetSymbolAddress failed", DPD_ECUDA);
   cudaStream_t s = (cudaStream_t)stream;

@@ -50,6 +50,12 @@ struct dpd_system {
   int* d_out_id = nullptr;
   uint8_t* d_out_type = nullptr;
   int out_cap = 0;
+  // staging for host inputs of dpd_set_particles (pos and vel, ids, types, id check)
+  float4* d_in4 = nullptr;
+  int* d_in_id = nullptr;
+  uint8_t* d_in_type = nullptr;
+  uint32_t* d_seen = nullptr;
+  int in_cap = 0;
   // profile accumulators and diagnostics
   double* d_prof = nullptr;
   int prof_cap = 0, prof_axis = 2, prof_nbins = 0;

@@ -149,7 +149,7 @@ def dpd_step(h, nsteps: int):
     return _check(h, load_library().dpd_step(h, int(nsteps)))
 
 
-PHASES = ("integrate", "scan", "sort", "force")
+PHASES = ("integrate", "scan", "scatter", "cell_sort", "gather", "force_pairs", "force_finish")
 
 
 def dpd_time_phases(h, nsteps: int) -> dict:

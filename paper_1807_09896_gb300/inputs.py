@@ -186,6 +186,37 @@ def _sphere_distance(pts, cs, rs, L):
     return d
 
 
+# Beyond this distance from every surface tanh(d / (sqrt(2) eps)) rounds to 1 in binary32.
+_PHI_SATURATION_DISTANCE = 7.0
+
+
+def _sphere_phi(L, cs, rs, h):
+    """phi = tanh(d / (sqrt(2) eps)) on the periodic node grid, d the signed distance
+    to the union of the spheres.  Each sphere only updates the nodes within
+    _PHI_SATURATION_DISTANCE of its surface (every other node rounds to phi = 1 in
+    binary32 whatever its distance), with the same arithmetic per node as
+    _sphere_distance, so the grid equals the all-spheres evaluation bit for bit."""
+    n = int(round(L / h))
+    ax = np.arange(n) * h
+    dist = np.full((n, n, n), np.inf)  # (z, y, x)
+    for c, r in zip(cs, rs):
+        reach = r + _PHI_SATURATION_DISTANCE
+        sel = []
+        for a in range(3):
+            lo = int(math.floor((c[a] - reach) / h))
+            hi = int(math.ceil((c[a] + reach) / h))
+            idx = np.arange(lo, hi + 1) % n if hi - lo + 1 < n else np.arange(n)
+            idx = np.unique(idx)
+            dd = ax[idx] - c[a]
+            dd -= L * np.round(dd / L)
+            sel.append((idx, dd * dd))
+        (ix, dx2), (iy, dy2), (iz, dz2) = sel
+        d = np.sqrt((dx2[None, None, :] + dy2[None, :, None]) + dz2[:, None, None]) - r
+        sub = np.ix_(iz, iy, ix)
+        dist[sub] = np.minimum(dist[sub], d)
+    return _phi_from_distance(dist)
+
+
 def sphere_pack(L: float, nspheres: int, rmin: float, rmax: float, rho: float = 3.0,
                 layer: float = 1.0, kBT: float = 1.0, seed: int = 0,
                 h: float = GRID_H) -> Workload:
@@ -193,14 +224,7 @@ def sphere_pack(L: float, nspheres: int, rmin: float, rmax: float, rho: float = 
     box = (float(L),) * 3
     rng = np.random.default_rng(seed)
     cs, rs = _place_spheres(L, nspheres, rmin, rmax, rng)
-    n = int(round(L / h))
-    phi = np.empty((n, n, n), np.float32)
-    ax = np.arange(n) * h
-    yy, xx = np.meshgrid(ax, ax, indexing="ij")
-    plane = np.stack([xx.ravel(), yy.ravel(), np.zeros(xx.size)], axis=1)
-    for k in range(n):
-        plane[:, 2] = k * h
-        phi[k] = _phi_from_distance(_sphere_distance(plane, cs, rs, L)).reshape(n, n)
+    phi = _sphere_phi(L, cs, rs, h)
     ncand = int(round(rho * L ** 3))
     cand = rng.uniform(0, L, size=(ncand, 3))
     d = np.empty(ncand)
