@@ -53,19 +53,19 @@ BYTES_PER_PARTICLE_STEP = 310
 # Algorithmic bytes of each phase's kernel(s), per fluid particle, per solid
 # particle and per cell (minimal traffic: every array the kernel must read or write,
 # once).  integrate: pos, vel, frc in; pos, vel, vt, key, rank out (a resting solid
-# particle: pos in, key and rank out).  scan: count read twice, start written, count
-# cleared.  scatter: key, rank, start in; perm out.  cell_sort: perm in and out,
-# start in.  gather: perm, then pos, vt, vel in and out.  force_pairs: full shell
-# pos, vt, vel in, frc and vel out; half shell pos, vt in and 24 B of fixed-point
-# sums.  force_finish: sums in and cleared, pos, vt, vel in, frc and vel out.
+# particle: pos in, key and rank out); after a half-shell force the 24 B of
+# fixed-point sums replace frc and are cleared (+32 B).  scan: count read twice,
+# start written, count cleared.  scatter: key, rank, start in; perm out.  cell_sort:
+# perm in and out, start in.  gather: perm, then pos, vt, vel in and out.
+# force_pairs: full shell pos, vt, vel in, frc and vel out; half shell pos, vt in and
+# 24 B of fixed-point sums.  (A step launches no finish pass: the drift does its work.)
 PHASE_BYTES = {
-    "integrate": (104, 24, 0),
+    "integrate": {False: (104, 24, 0), True: (136, 24, 0)},
     "scan": (0, 0, 16),
     "scatter": (12, 12, 4),
     "cell_sort": (8, 8, 8),
     "gather": (100, 100, 0),
     "force_pairs": {False: (80, 16, 0), True: (56, 32, 0)},
-    "force_finish": (128, 16, 0),
 }
 SM_COUNT_GB300 = 152
 LANES_PER_SM = 128
@@ -184,11 +184,11 @@ def per_kernel_roofline(ph, newton3, n_fluid, n_solid, ncells, hbm_peak, hbm_src
     phase's mean CUDA-event time."""
     out = {}
     for name, ms in ph.items():
+        if name not in PHASE_BYTES or ms <= 0.0:
+            continue
         spec = PHASE_BYTES[name]
         if isinstance(spec, dict):
             spec = spec[newton3]
-        if ms <= 0.0 or (name == "force_finish" and not newton3):
-            continue
         bpf, bps, bpc = spec
         nbytes = bpf * n_fluid + bps * n_solid + bpc * ncells
         gbs = nbytes / (ms * 1e-3) / 1e9
@@ -629,7 +629,7 @@ def run_ours(args):
     # phase durations with CUDA events on the library's stream (same launches, no graph)
     nph = min(args.steps, 50)
     ph = dpd.dpd_time_phases(s.h, nph)
-    force_ms = ph["force_pairs"] + ph["force_finish"]
+    force_ms = ph["force_pairs"]
     # the unit of work is fixed per particle-step (27 cells of candidates, every pair in
     # r_c), whichever algorithm runs; the half shell's own count is reported beside it
     cand = 27 * 3.0                    # 27 cells of unit volume at rho = 3
@@ -711,8 +711,8 @@ def run_ours(args):
                           f"timing; repeats {min(rep_ms):.4f}-{max(rep_ms):.4f} ms)",
             },
             "roofline": {
-                "kernel": ("k_force_n3 + k_force_finish (half-shell pair force, fixed-point sums, "
-                           "closing half-kick)" if newton3 else
+                "kernel": ("k_force_n3 (half-shell pair force, fixed-point sums; the next drift "
+                           "converts them and completes the closing kick)" if newton3 else
                            "k_force (full-shell pair force + closing half-kick)"),
                 "bound": "alu",
                 "ops_per_particle": ops_unit, "ops_per_particle_own_algorithm": ops_own,

@@ -65,7 +65,7 @@ enum {
   DPD_ESTATE = -4,   /* call out of order (e.g. dpd_step before dpd_set_particles) */
   DPD_ELOST = -5,    /* a fluid particle was found at phi < 0 */
   DPD_EBAND = -6,    /* a drift exceeded the band margin of the reflection test */
-  DPD_ETIMEOUT = -7, /* reserved: a bounded device wait gave up */
+  DPD_ETIMEOUT = -7, /* a bounded device wait gave up (the cell scan's look-back) */
   DPD_ENAN = -8,     /* a non-finite position, velocity or force appeared */
   DPD_EOVERFLOW = -9 /* a size limit was exceeded (e.g. a cell holds too many particles) */
 };
@@ -113,7 +113,9 @@ int dpd_init_particles(dpd_t* h, uint64_t seed, double solid_layer);
  * velocities, id a permutation of 0..n-1, type 0 fluid / 1 solid.  Computes the
  * pair force f(0) at the given state (predicted velocity = v).  Solid
  * velocities are ignored (they move with the wall velocity).  Fails with DPD_ELOST if a fluid
- * particle sits at phi < 0.  The step counter is kept (see option "step"). */
+ * particle sits inside the solid, at phi < -1e-4 (a margin for the rounding of binary32
+ * positions: a step stores positions rounded, and one just outside the wall can read
+ * a phase field a few 1e-6 below zero).  The step counter is kept (see option "step"). */
 int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, const int* id,
                       const uint8_t* type, int where);
 
@@ -249,9 +251,14 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * parameters), "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
  * default 20), "force_variant" (launch shape of the pair-force kernel, see
- * dpd_autotune).  Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
+ * dpd_autotune), "scan_stall_tile" (a test hook, default -1: tile k >= 0 of the
+ * single-pass cell scan publishes nothing, so the tiles after it give up waiting
+ * and the step returns DPD_ETIMEOUT; the force kernels skip that step and the state stays
+ * invalid until the next dpd_set_particles).
+ * Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
  * enqueued by stepping calls so far), "kernels_per_step", "force_variants",
- * "force_newton3" (1 if the current shape evaluates each pair once). */
+ * "force_newton3" (1 if the current shape evaluates each pair once), "scan_tiles"
+ * (tiles of 8192 cells in the cell scan). */
 int dpd_set_option(dpd_t* h, const char* key, double value);
 int dpd_get_option(dpd_t* h, const char* key, double* value);
 
@@ -287,6 +294,29 @@ int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
 int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
                        double wall_hi, int nbins, double bin_width, const double* target,
                        int tie_sigma, double* loss_out, double grad[3]);
+
+/* dpd_adjoint_window, plus a record of its pieces, so that each segment of the
+ * window can be checked on its own (the paper has no counterpart).  Host outputs,
+ * each may be NULL; nseg = nsteps / ckpt_every, n the particle count:
+ * ckpt      (nseg + 1) x n x 12 floats: the state at each checkpoint (steps
+ *           0, K, 2K, ...), per particle in id order: position (x, y, z, tag),
+ *           velocity (x, y, z, 1 if reflected in the step that produced it),
+ *           pair force (x, y, z, 0).
+ * adj       (nseg + 1) x n x 12 floats, same layout: the adjoint of that state
+ *           (dL/d position, dL/d velocity, dL/d force, each with an unused 4th
+ *           float), L linearised at the forward trajectory; it includes the
+ *           loss terms of the state itself and of every later state.
+ * seg_grad  nseg x 3 doubles: dL/d(a_fs, gamma, g_x) accumulated while reversing
+ *           segment k (segment 0 includes the dependence of f(0) on the
+ *           parameters); they add up to grad.
+ * coef      nbins floats: dL/d(sum of vx in bin b over the window), i.e.
+ *           2 (u_b - target_b) / count_b (0 for bins never visited).
+ * seg_step  nseg + 1 step counters (noise counter word 2) of the checkpoints.
+ * Everything else as dpd_adjoint_window. */
+int dpd_adjoint_window_record(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
+                              double wall_hi, int nbins, double bin_width, const double* target,
+                              int tie_sigma, double* loss_out, double grad[3], float* ckpt,
+                              float* adj, double* seg_grad, float* coef, uint32_t* seg_step);
 
 /* ---- Batches: many independent systems advanced together ------------------
  * The paper has no counterpart (it runs one system at a time); this is the

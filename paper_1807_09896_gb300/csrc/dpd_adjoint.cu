@@ -141,10 +141,11 @@ __global__ void __launch_bounds__(128)
 k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restrict__ vt,
             const uint32_t* __restrict__ start, int n, uint32_t step, const float4* __restrict__ rbar,
             const float4* __restrict__ vbar, const float4* __restrict__ fbar, float4* Rb, float4* Vb,
-            float tie_coef, double* theta) {
+            float tie_coef, double* theta, const DevCounters* ctr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double ta = 0.0, tg = 0.0;
-  if (i < n) {
+  // cell starts left by a timed-out scan are not a valid prefix (the status reports it)
+  if (i < n && !scan_failed(ctr)) {
     const float4 pi = pos[i];
     if (is_solid(pi.w)) {
       Rb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -311,6 +312,20 @@ __global__ void k_seed(const float4* pos, int n, WallBins B, const float* coef, 
   vbar[i] = v;
 }
 
+// Three per-particle arrays of one state (in that state's cell order) into id order:
+// out[12 id .. 12 id + 11] = a[i], b[i], c[i], ids from the tags of key_pos.
+__global__ void k_unsort3(const float4* __restrict__ key_pos, const float4* __restrict__ a,
+                          const float4* __restrict__ b, const float4* __restrict__ c, int n,
+                          float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t id = id_of(key_pos[i].w);
+  if (id >= (uint32_t)n) return;
+  out[3 * (size_t)id + 0] = a[i];
+  out[3 * (size_t)id + 1] = b[i];
+  out[3 * (size_t)id + 2] = c[i];
+}
+
 struct Buf {
   std::vector<void*> ptrs;
   ~Buf() {
@@ -349,9 +364,20 @@ inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 using dpd::Arrays;
 using dpd::DevCounters;
 
-extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
-                                  double wall_hi, int nbins, double bin_width, const double* target,
-                                  int tie_sigma, double* loss_out, double grad[3]) {
+namespace {
+// Where dpd_adjoint_window_record puts its record (host memory, entries may be NULL).
+struct AdjointRecord {
+  float* ckpt;
+  float* adj;
+  double* seg_grad;
+  float* coef;
+  uint32_t* seg_step;
+};
+}  // namespace
+
+static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
+                          double wall_hi, int nbins, double bin_width, const double* target,
+                          int tie_sigma, double* loss_out, double grad[3], const AdjointRecord* rec) {
   using namespace dpd;
   if (!h || !target || !grad) return DPD_EINVAL;
   if (!h->loaded) return afail(h, DPD_ESTATE, "no valid particle state (call dpd_set_particles)");
@@ -367,6 +393,9 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
     return afail(h, DPD_EINVAL, "tying sigma to gamma needs kBT > 0 and gamma > 0");
   Engine& E = h->E;
   if (E.h_ctr[0].status) return engine_status_code(E, E.h_ctr[0].status);
+  // the window records complete states (force in frc, velocity kicked) after every
+  // step: steps here run their finish pass
+  engine_settle(E);
   // Eq. 8, sigma^2 = 2 gamma kBT: the forward window runs with the sigma that the
   // gradient assumes (the system keeps it)
   if (tie_sigma) h->sigma = std::sqrt(2.0 * h->gamma * h->kBT);
@@ -459,7 +488,7 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
   ACU(copy_state(ck[0], E.arr[E.cur]));
   ACU(cudaMemcpyAsync(start0, E.cl.start, start_bytes, cudaMemcpyDeviceToDevice, st));
   for (int s = 1; s <= nsteps; ++s) {
-    engine_enqueue_step(E);
+    engine_enqueue_step(E, true);
     const Arrays& A = E.arr[E.cur];
     k_wall_profile<<<nblk(n, 256), 256, 0, st>>>(A.pos, A.vel, n, B, acc);
     if (s % K == 0) ACU(copy_state(ck[s / K], A));
@@ -482,6 +511,22 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
     hcoef[b] = (float)(2.0 * (u - target[b]) / cnt);
   }
   ACU(cudaMemcpyAsync(coef, hcoef.data(), sizeof(float) * nbins, cudaMemcpyHostToDevice, st));
+  float4* stage = nullptr;  // id-ordered copy of three per-particle arrays
+  const size_t rec_floats = (size_t)12 * n;
+  if (rec) {
+    ACU(buf.alloc(&stage, 3 * (size_t)n));
+    if (rec->coef) memcpy(rec->coef, hcoef.data(), sizeof(float) * nbins);
+    if (rec->seg_step)
+      for (int q2 = 0; q2 <= nseg; ++q2) rec->seg_step[q2] = step0 + (uint32_t)(q2 * K);
+    if (rec->ckpt)
+      for (int q2 = 0; q2 <= nseg; ++q2) {
+        k_unsort3<<<nblk(n, 256), 256, 0, st>>>(ck[q2].pos, ck[q2].pos, ck[q2].vel, ck[q2].frc, n, stage);
+        ACU(cudaMemcpyAsync(rec->ckpt + q2 * rec_floats, stage, sizeof(float) * rec_floats,
+                            cudaMemcpyDeviceToHost, st));
+      }
+  }
+  // per-segment parameter gradient: theta after each segment's reversal
+  std::vector<double> theta_snap(3 * (size_t)(nseg + 1), 0.0);
   ACU(cudaMemsetAsync(theta, 0, 3 * sizeof(double), st));
   ACU(cudaMemsetAsync(zero4, 0, nf4, st));
 
@@ -493,13 +538,19 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
   ACU(cudaMemsetAsync(fb[q], 0, nf4, st));
   const float tie = tie_sigma ? (float)(h->kBT / h->sigma / std::sqrt(h->dt)) : 0.0f;
   for (int seg = nseg - 1; seg >= 0; --seg) {
+    if (rec && rec->adj) {
+      // the adjoint of the segment's end state (it includes that state's own loss term)
+      k_unsort3<<<nblk(n, 256), 256, 0, st>>>(ck[seg + 1].pos, rb[q], vb[q], fb[q], n, stage);
+      ACU(cudaMemcpyAsync(rec->adj + (size_t)(seg + 1) * rec_floats, stage, sizeof(float) * rec_floats,
+                          cudaMemcpyDeviceToHost, st));
+    }
     // recompute the segment, recording every step
     ACU(copy_state(E.arr[E.cur], ck[seg]));
     const uint32_t seg_step = step0 + (uint32_t)(seg * K);
     ACU(cudaMemcpyAsync(&E.d_ctr[0].step, &seg_step, sizeof seg_step, cudaMemcpyHostToDevice, st));
     ACU(copy_state(tape[0], ck[seg]));
     for (int k = 0; k < K; ++k) {
-      engine_enqueue_step(E);
+      engine_enqueue_step(E, true);
       ACU(copy_state(tape[k + 1], E.arr[E.cur]));
       ACU(cudaMemcpyAsync(tperm[k], E.cl.perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
       ACU(cudaMemcpyAsync(tstart[k], E.cl.start, sizeof(uint32_t) * ((size_t)E.ncells + 1),
@@ -511,23 +562,37 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
       const Arrays& An = tape[k + 1];
       const Arrays& Ao = tape[k];
       k_adj_force<<<nblk(n, 128), 128, 0, st>>>(P, An.pos, An.vt, tstart[k], n, step_new, rb[q], vb[q],
-                                                fb[q], Rb, Vb, tie, theta);
+                                                fb[q], Rb, Vb, tie, theta, E.d_ctr);
       const int s_old = seg * K + k;  // global index of the previous state
       k_adj_integrate<<<nblk(n, 256), 256, 0, st>>>(P, Ao.pos, Ao.vel, Ao.frc, An.pos, An.vt, tperm[k], n,
                                                     Rb, Vb, vb[q], rb[q ^ 1], vb[q ^ 1], fb[q ^ 1], B,
                                                     s_old >= 1 ? coef : nullptr, theta);
       q ^= 1;
     }
+    if (rec && rec->seg_grad && seg > 0) {
+      ACU(cudaMemcpyAsync(&theta_snap[3 * (size_t)seg], theta, 3 * sizeof(double),
+                          cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (rec && rec->adj) {
+    k_unsort3<<<nblk(n, 256), 256, 0, st>>>(ck[0].pos, rb[q], vb[q], fb[q], n, stage);
+    ACU(cudaMemcpyAsync(rec->adj, stage, sizeof(float) * rec_floats, cudaMemcpyDeviceToHost, st));
   }
   // f(0) = f(r0, v0): its parameter dependence, with F-bar = fbar(0) (no kick)
   {
     const Arrays& A0 = ck[0];
     k_adj_force<<<nblk(n, 128), 128, 0, st>>>(P, A0.pos, A0.vt, start0, n, step0, zero4, zero4,
-                                              fb[q], Rb, Vb, tie, theta);
+                                              fb[q], Rb, Vb, tie, theta, E.d_ctr);
   }
   ACU(cudaGetLastError());
   double th[3];
   ACU(cudaMemcpyAsync(th, theta, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // a recomputed segment whose scan timed out leaves its status (nothing else sets one:
+  // the forward window ran the same steps without error)
+  DevCounters ctr_bwd;
+  ACU(cudaMemcpyAsync(&ctr_bwd, E.d_ctr, sizeof ctr_bwd, cudaMemcpyDeviceToHost, st));
+  ACU(cudaStreamSynchronize(st));
+  if (ctr_bwd.status & ST_TIMEOUT) return engine_status_code(E, ctr_bwd.status);
   // ---- leave the system at the end of the window, as dpd_step would ----------
   ACU(copy_state(E.arr[E.cur], ck[nseg]));
   ACU(cudaMemcpyAsync(E.cl.start, start_end, start_bytes, cudaMemcpyDeviceToDevice, st));
@@ -539,6 +604,35 @@ extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis
   grad[0] = th[0];
   grad[1] = th[1];
   grad[2] = th[2];
+  if (rec && rec->seg_grad) {
+    // segment k's share: theta accumulated while reversing it (segment 0 also holds
+    // the dependence of f(0) on the parameters); snapshots were taken after the
+    // reversal of segments nseg-1 .. 1
+    for (int k2 = 0; k2 < 3; ++k2) theta_snap[3 * (size_t)nseg + k2] = 0.0;
+    for (int k2 = 0; k2 < 3; ++k2) theta_snap[k2] = th[k2];
+    for (int seg = 0; seg < nseg; ++seg) {
+      const double* after = &theta_snap[3 * (size_t)seg];
+      const double* before = &theta_snap[3 * (size_t)(seg + 1)];
+      for (int k2 = 0; k2 < 3; ++k2) rec->seg_grad[3 * seg + k2] = after[k2] - before[k2];
+    }
+  }
   if (loss_out) *loss_out = L;
   return DPD_OK;
+}
+
+extern "C" int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
+                                  double wall_hi, int nbins, double bin_width, const double* target,
+                                  int tie_sigma, double* loss_out, double grad[3]) {
+  return adjoint_window(h, nsteps, ckpt_every, axis, wall_lo, wall_hi, nbins, bin_width, target,
+                        tie_sigma, loss_out, grad, nullptr);
+}
+
+extern "C" int dpd_adjoint_window_record(dpd_t* h, int nsteps, int ckpt_every, int axis,
+                                         double wall_lo, double wall_hi, int nbins, double bin_width,
+                                         const double* target, int tie_sigma, double* loss_out,
+                                         double grad[3], float* ckpt, float* adj, double* seg_grad,
+                                         float* coef, uint32_t* seg_step) {
+  const AdjointRecord rec{ckpt, adj, seg_grad, coef, seg_step};
+  return adjoint_window(h, nsteps, ckpt_every, axis, wall_lo, wall_hi, nbins, bin_width, target,
+                        tie_sigma, loss_out, grad, &rec);
 }

@@ -123,6 +123,7 @@ static int read_status(dpd_t* h, uint32_t* st) {
 
 static int add_profile_sample(dpd_t* h) {
   if (h->prof_nbins <= 0) return DPD_OK;
+  dpd::engine_settle(h->E);
   const float lo = (float)h->prof_lo;
   const float inv_w = (float)((double)h->prof_nbins / (h->prof_hi - h->prof_lo));
   const Arrays& A = h->E.arr[h->E.cur];
@@ -244,7 +245,7 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
   int nf = 0;
   // Stage the inputs on the device (staging buffers grow only and are kept).
   const bool host = where == DPD_HOST;
-  if (n > h->in_cap) {
+  if (n > h->in_cap || !h->d_seen) {
     cudaFree(h->d_in4);
     cudaFree(h->d_in_id);
     cudaFree(h->d_in_type);
@@ -254,11 +255,12 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
     h->d_in_type = nullptr;
     h->d_seen = nullptr;
     h->in_cap = 0;
-    CU(h, dev_alloc(&h->d_in4, (size_t)2 * n));
-    CU(h, dev_alloc(&h->d_in_id, n));
-    CU(h, dev_alloc(&h->d_in_type, n));
-    CU(h, dev_alloc(&h->d_seen, n));
-    h->in_cap = n;
+    const int cap = n > 1 ? n : 1;
+    CU(h, dev_alloc(&h->d_in4, (size_t)2 * cap));
+    CU(h, dev_alloc(&h->d_in_id, cap));
+    CU(h, dev_alloc(&h->d_in_type, cap));
+    CU(h, dev_alloc(&h->d_seen, cap));
+    h->in_cap = cap;
   }
   float4 *in_pos = nullptr, *in_vel = nullptr;
   int* in_id = nullptr;
@@ -284,6 +286,8 @@ int dpd_set_particles(dpd_t* h, int n, const float* pos4, const float* vel4, con
     CU(h, cudaMemcpyAsync(host_type.data(), type, n, cudaMemcpyDeviceToHost, E.stream));
   }
   CU(h, cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (n > 0 ? n : 1), E.stream));
+  // the fixed-point sums start empty (their layout depends on n)
+  if (n > 0) CU(h, cudaMemsetAsync(E.facc, 0, sizeof(unsigned long long) * 3 * (size_t)n, E.stream));
   // Status is cleared; the step counter is kept.
   CU(h, cudaMemsetAsync(&E.d_ctr[0].status, 0, sizeof(uint32_t), E.stream));
   E.cur = 0;
@@ -374,6 +378,7 @@ int dpd_get_state(dpd_t* h, float* pos4, float* vel4, float* force4, int* id, ui
   if (!h->loaded) return fail(h, DPD_ESTATE, "no valid particle state (call dpd_set_particles)");
   dpd::Engine& E = h->E;
   const int n = E.n;
+  dpd::engine_settle(E);
   const Arrays& A = E.arr[E.cur];
   if (where == DPD_DEVICE) {
     dpd::launch_unsort(A, n, (float4*)pos4, (float4*)vel4, (float4*)force4, id, type, E.stream);
@@ -436,6 +441,7 @@ int dpd_get_stats(dpd_t* h, double out[8]) {
   if (!h || !out) return DPD_EINVAL;
   dpd::Engine& E = h->E;
   CU(h, cudaMemsetAsync(h->d_stats, 0, 8 * sizeof(double), E.stream));
+  if (h->loaded) dpd::engine_settle(E);
   const Arrays& A = E.arr[E.cur];
   if (h->loaded) dpd::launch_stats(A.pos, A.vel, E.n, h->d_stats, E.stream);
   CU(h, cudaGetLastError());
@@ -538,6 +544,10 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     if (v < 2 || v > 1000 || v != std::floor(v) || ((int)v & 1))
       return fail(h, DPD_EINVAL, "graph_steps must be an even number in [2, 1000]");
     E.graph_steps = (int)v;
+  } else if (k == "scan_stall_tile") {
+    if (v < -1 || v != std::floor(v) || v > 1e9)
+      return fail(h, DPD_EINVAL, "scan_stall_tile must be -1 or a tile index");
+    E.scan_stall_tile = (int)v;
   } else {
     return fail(h, DPD_EINVAL, "unknown option '%s'", key);
   }
@@ -579,7 +589,9 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "kernels_per_step") *v = dpd::engine_kernels_per_step(E);
   else if (k == "force_variant") *v = E.force_variant;
   else if (k == "force_variants") *v = dpd::force_variants();
-  else if (k == "force_newton3") *v = dpd::force_variant_kernels(E.force_variant) == 2;
+  else if (k == "force_newton3") *v = dpd::force_variant_newton3(E.force_variant);
+  else if (k == "scan_stall_tile") *v = E.scan_stall_tile;
+  else if (k == "scan_tiles") *v = dpd::scan_blocks(h->ncells);
   else return fail(h, DPD_EINVAL, "unknown option '%s'", key);
   return DPD_OK;
 }

@@ -115,7 +115,8 @@ int dpd_batch_create(dpd_batch_t** out, int nsys, dpd_t* const* systems) {
     S.part_off = poff;
     S.n = (uint32_t)h->E.n;
     S.pad = 0;
-    // bring the system's state into the batch (its own stream first)
+    // bring the system's state into the batch (complete, from its own stream)
+    dpd::engine_settle(h->E);
     cudaStreamSynchronize(h->E.stream);
     const Arrays src = h->E.arr[h->E.cur];
     const Arrays dst = offset(E.arr[0], poff);
@@ -193,6 +194,7 @@ int dpd_batch_get_state(dpd_batch_t* b, int k, float* pos4, float* vel4, float* 
   if (k < 0 || k >= E.nsys) return bfail(b, DPD_EINVAL, "system index %d out of range", k);
   if (where != DPD_HOST && where != DPD_DEVICE) return bfail(b, DPD_EINVAL, "bad `where`");
   const int n = (int)E.h_sys[k].n;
+  dpd::engine_settle(E);
   const Arrays A = offset(E.arr[E.cur], E.h_sys[k].part_off);
   if (where == DPD_DEVICE) {
     dpd::launch_unsort(A, n, (float4*)pos4, (float4*)vel4, (float4*)force4, id, type, E.stream);
@@ -220,6 +222,7 @@ int dpd_batch_get_stats(dpd_batch_t* b, int k, double out[8]) {
   dpd::Engine& E = b->E;
   if (k < 0 || k >= E.nsys) return bfail(b, DPD_EINVAL, "system index %d out of range", k);
   BCU(b, cudaMemsetAsync(b->d_stats, 0, 8 * sizeof(double), E.stream));
+  dpd::engine_settle(E);
   const Arrays A = offset(E.arr[E.cur], E.h_sys[k].part_off);
   dpd::launch_stats(A.pos, A.vel, (int)E.h_sys[k].n, b->d_stats, E.stream);
   BCU(b, cudaGetLastError());
@@ -265,7 +268,7 @@ int dpd_batch_get_option(dpd_batch_t* b, const char* key, double* v) {
   else if (k == "graph_steps") *v = E.graph_steps;
   else if (k == "force_variant") *v = E.force_variant;
   else if (k == "force_variants") *v = dpd::force_variants();
-  else if (k == "force_newton3") *v = dpd::force_variant_kernels(E.force_variant) == 2;
+  else if (k == "force_newton3") *v = dpd::force_variant_newton3(E.force_variant);
   else if (k == "kernel_launches") *v = (double)E.launches;
   else if (k == "kernels_per_step") *v = dpd::engine_kernels_per_step(E);
   else if (k == "nsys") *v = E.nsys;

@@ -4,8 +4,11 @@
 // Particle data live as structure-of-arrays of float4 in cell order:
 //   pos  {x, y, z, tag}   tag = bit pattern of (id | solid << 31)
 //   vt   {vtx, vty, vtz, reflected flag}   predicted velocity of the step
-//   vel  {vx, vy, vz, 0}  velocity v(t)
+//   vel  {vx, vy, vz, reflected flag}  velocity v(t)
 //   frc  {fx, fy, fz, 0}  pair force f(t) (body force not included)
+// Between the steps of a Newton's-third-law force shape the force is not in frc but
+// in 64-bit fixed-point sums, and vel still lacks the second half of the closing
+// kick; DevCounters::sums_pending says so (see the drift kernel).
 #pragma once
 
 #include <cstdint>
@@ -23,6 +26,7 @@ enum : uint32_t {
   ST_LOST = 4u,      // fluid particle at phi < 0
   ST_OVERFLOW = 8u,  // a cell exceeded the per-cell sort capacity
   ST_BADID = 16u,    // ids are not a permutation of 0..n-1
+  ST_TIMEOUT = 32u,  // a bounded device wait gave up (the cell scan's look-back)
 };
 
 struct DevCounters {
@@ -30,7 +34,47 @@ struct DevCounters {
   uint32_t step;                 // noise counter of the most recent force evaluation
   unsigned long long reflections;
   unsigned long long fallbacks;
+  // 1 while the force of the current state is still in the fixed-point pair sums
+  // and the second half of its closing kick has not been applied (the state a
+  // Newton's-third-law force kernel leaves); the next drift completes both
+  uint32_t sums_pending;
+  uint32_t pad;
 };
+
+// True when a timed-out cell scan left the cell starts unusable: kernels that index
+// through them do nothing (the status makes the step report DPD_ETIMEOUT).
+__device__ __forceinline__ bool scan_failed(const DevCounters* ctr) {
+  return (ctr->status & ST_TIMEOUT) != 0u;
+}
+
+// Fixed-point pair sums of the Newton's-third-law force shapes: 2^32 units per
+// force unit, one array of n per component, holding the shares -f_ij handed to
+// each particle by its partners.  The particle's own share (the binary32 sum of the
+// pairs it evaluated) is stored in frc and added as one more integer term when the
+// sums are read.
+constexpr float kFixScale = 4294967296.0f;        // 2^32
+constexpr float kFixInvF = 1.0f / 4294967296.0f;  // 2^-32
+
+__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * kFixScale); }
+
+// The force of particle i: its partners' fixed-point sums plus its own share, one
+// rounding from the exact integer (the power-of-two scale is exact).  Integer sums
+// do not depend on the order of their terms, so neither does the result.
+__device__ __forceinline__ float3 fixed_sum_force(const unsigned long long* facc, size_t n, size_t i,
+                                                  float4 own) {
+  const long long x = (long long)facc[i] + to_fixed(own.x);
+  const long long y = (long long)facc[n + i] + to_fixed(own.y);
+  const long long z = (long long)facc[2 * n + i] + to_fixed(own.z);
+  return make_float3(__ll2float_rn(x) * kFixInvF, __ll2float_rn(y) * kFixInvF,
+                     __ll2float_rn(z) * kFixInvF);
+}
+
+// Mark systems 0..nsys-1 as holding (1) or not holding (0) pending sums; grid-stride,
+// so that every system is marked whatever the launch size.
+__device__ __forceinline__ void mark_sums_pending(DevCounters* ctrs, int nsys, uint32_t v) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsys; k += gridDim.x * blockDim.x)
+    ctrs[k].sums_pending = v;
+}
 
 // Everything a step kernel needs, passed by value.
 struct StepParams {
@@ -98,7 +142,7 @@ __device__ __forceinline__ int sys_of(const SysDesc* __restrict__ S, int nsys, u
 struct Arrays {
   float4* pos;
   float4* vt;
-  float4* vel;
+  float4* vel;  // .w: 1 if the particle was reflected in the step that produced it
   float4* frc;
 };
 
@@ -108,7 +152,11 @@ struct CellList {
   uint32_t* count;  // particles per cell (zeroed by the scan)
   uint32_t* start;  // exclusive prefix of count, ncells + 1 entries
   uint32_t* perm;   // new position -> old position
-  uint32_t* blocksum;
+  // single-pass scan: one published word per tile of cells, and the ticket counter
+  // that numbers the tiles in the order their blocks start (never reset between
+  // launches: ticket / tiles is the launch's epoch)
+  unsigned long long* tile;
+  unsigned long long* ticket;
 };
 
 __device__ __forceinline__ uint32_t tag_of(float w) { return __float_as_uint(w); }

@@ -60,8 +60,10 @@ static void free_particle_buffers(Engine& E) {
 static void free_cell_buffers(Engine& E) {
   cudaFree(E.cl.count);
   cudaFree(E.cl.start);
-  cudaFree(E.cl.blocksum);
-  E.cl.count = E.cl.start = E.cl.blocksum = nullptr;
+  cudaFree(E.cl.tile);
+  cudaFree(E.cl.ticket);
+  E.cl.count = E.cl.start = nullptr;
+  E.cl.tile = E.cl.ticket = nullptr;
   E.cell_cap = 0;
 }
 
@@ -101,8 +103,16 @@ int engine_reserve(Engine& E, int nsys, int n, int ncells) {
     free_cell_buffers(E);
     ECU(E, dev_alloc(&E.cl.count, ncells));
     ECU(E, dev_alloc(&E.cl.start, (size_t)ncells + 1));
-    ECU(E, dev_alloc(&E.cl.blocksum, scan_blocks(ncells)));
+    ECU(E, dev_alloc(&E.cl.tile, scan_blocks(ncells)));
+    ECU(E, dev_alloc(&E.cl.ticket, 1));
+    ECU(E, cudaMemsetAsync(E.cl.tile, 0, sizeof(unsigned long long) * scan_blocks(ncells), E.stream));
     E.cell_cap = ncells;
+  }
+  if (ncells != E.ncells) {
+    // the ticket numbers launches of one tile count: restart it, and clear the published
+    // words, whose epochs would otherwise repeat
+    ECU(E, cudaMemsetAsync(E.cl.ticket, 0, sizeof(unsigned long long), E.stream));
+    ECU(E, cudaMemsetAsync(E.cl.tile, 0, sizeof(unsigned long long) * scan_blocks(ncells), E.stream));
   }
   if (n > E.cap) {
     engine_free_graphs(E);
@@ -137,34 +147,49 @@ int engine_upload_sys(Engine& E) {
 
 void engine_enqueue_sort(Engine& E) {
   launch_key(E.d_sys, E.nsys, E.arr[E.cur], E.cl, E.n, E.stream);
-  launch_scan(E.cl, E.ncells, E.n, E.stream);
+  launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
   launch_sort(E.cl, E.arr[E.cur], E.arr[E.cur ^ 1], E.n, E.ncells, E.d_ctr, E.stream);
   E.cur ^= 1;
 }
 
 int engine_kernels_per_step(const Engine& E) {
-  const int rest = E.n > 0 ? kKernelsPerStepSort + force_variant_kernels(E.force_variant) : 0;
+  const int rest = E.n > 0 ? kKernelsPerStepSort + 1 : 0;
   return integrate_kernels(E.n, E.nsys) + scan_kernels(E.ncells) + rest;
 }
 
 void engine_enqueue_force(Engine& E, int kick) {
   launch_force(E.h_sys[0].P, E.d_sys, E.nsys, E.arr[E.cur], E.cl.start, E.facc, E.n, E.d_ctr, kick,
                E.force_variant, E.stream);
+  E.sums_pending = false;
 }
 
-// One step from arr[c] into arr[c ^ 1] (does not touch E.cur).
-static void enqueue_step_from(Engine& E, int c) {
+void engine_settle(Engine& E) {
+  if (!E.sums_pending) return;
+  launch_force_finish(E.h_sys[0].P, E.d_sys, E.nsys, E.arr[E.cur], E.facc, E.n, E.d_ctr, 1, E.stream);
+  E.launches += 1;
+  E.sums_pending = false;
+}
+
+// One step from arr[c] into arr[c ^ 1] (does not touch E.cur).  The drift completes
+// whatever the previous step left pending (it reads the device flag).
+static void enqueue_step_from(Engine& E, int c, bool finish) {
   const Arrays& A = E.arr[c];
   const Arrays& B = E.arr[c ^ 1];
-  launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
-  launch_scan(E.cl, E.ncells, E.n, E.stream);
+  launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.n, E.d_ctr, E.stream);
+  launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
   launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
-  launch_force(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
-               E.force_variant, E.stream);
+  launch_force_pairs(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
+                     E.force_variant, E.stream);
+  E.sums_pending = force_variant_newton3(E.force_variant);
+  if (finish && E.sums_pending) {
+    launch_force_finish(E.h_sys[0].P, E.d_sys, E.nsys, B, E.facc, E.n, E.d_ctr, 1, E.stream);
+    E.launches += 1;
+    E.sums_pending = false;
+  }
 }
 
-void engine_enqueue_step(Engine& E) {
-  enqueue_step_from(E, E.cur);
+void engine_enqueue_step(Engine& E, bool finish) {
+  enqueue_step_from(E, E.cur, finish);
   E.cur ^= 1;
   E.launches += engine_kernels_per_step(E);
 }
@@ -174,7 +199,7 @@ static int build_graph(Engine& E, int c) {
   ECU(E, cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal));
   int cc = c;
   for (int k = 0; k < E.graph_steps; ++k) {
-    enqueue_step_from(E, cc);
+    enqueue_step_from(E, cc, false);
     cc ^= 1;
   }
   cudaError_t e = cudaStreamEndCapture(E.stream, &g);
@@ -233,9 +258,9 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
     const Arrays& A = E.arr[E.cur];
     const Arrays& B = E.arr[E.cur ^ 1];
     cudaEventRecord(ev[0], E.stream);
-    launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.n, E.d_ctr, E.stream);
+    launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.n, E.d_ctr, E.stream);
     cudaEventRecord(ev[1], E.stream);
-    launch_scan(E.cl, E.ncells, E.n, E.stream);
+    launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
     cudaEventRecord(ev[2], E.stream);
     launch_scatter(E.cl, E.n, E.d_ctr, E.stream);
     cudaEventRecord(ev[3], E.stream);
@@ -245,9 +270,10 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
     cudaEventRecord(ev[5], E.stream);
     launch_force_pairs(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
                        E.force_variant, E.stream);
+    E.sums_pending = force_variant_newton3(E.force_variant);
     cudaEventRecord(ev[6], E.stream);
-    launch_force_finish(E.h_sys[0].P, E.d_sys, E.nsys, B, E.facc, E.n, E.d_ctr, 1, E.force_variant,
-                        E.stream);
+    // a step launches no finish pass (the next drift does its work): the phase stays
+    // in the table, empty, so that the phases of older builds can be compared
     cudaEventRecord(ev[DPD_NPHASES], E.stream);
     E.launches += engine_kernels_per_step(E);
     E.cur ^= 1;
@@ -271,7 +297,9 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
 int engine_autotune(Engine& E, int nsteps, double* ms_per_variant, int* chosen) {
   const int nv = force_variants();
   // The timing steps must leave no trace: the shapes of the two force algorithms
-  // round differently, so the state and counters are kept and put back afterwards.
+  // round differently, so the state and counters are kept and put back afterwards
+  // (from a complete state: no sums pending).
+  engine_settle(E);
   Arrays keep{};
   DevCounters* keep_ctr = nullptr;
   const size_t n = (size_t)E.n;
@@ -299,11 +327,15 @@ int engine_autotune(Engine& E, int nsteps, double* ms_per_variant, int* chosen) 
     double ms[DPD_NPHASES];
     rc = engine_time_phases(E, 1, ms);  // warm-up of this shape
     if (rc == DPD_OK) rc = engine_time_phases(E, nsteps, ms);
+    engine_settle(E);
     if (rc != DPD_OK) break;
-    const double force_ms = ms[DPD_PHASE_FORCE] + ms[DPD_PHASE_FINISH];
-    if (ms_per_variant) ms_per_variant[v] = force_ms;
-    if (force_ms < best_ms) {
-      best_ms = force_ms;
+    // whole steps: the Newton's-third-law shapes move the conversion of their sums
+    // into the next drift
+    double step_ms = 0.0;
+    for (int q = 0; q < DPD_NPHASES; ++q) step_ms += ms[q];
+    if (ms_per_variant) ms_per_variant[v] = step_ms;
+    if (step_ms < best_ms) {
+      best_ms = step_ms;
       best = v;
     }
   }
@@ -343,6 +375,10 @@ int engine_status_code(Engine& E, uint32_t st) {
   if (st & ST_BADID) return engine_fail(E, DPD_EINVAL, "ids are not a permutation of 0..n-1");
   if (st & ST_OVERFLOW)
     return engine_fail(E, DPD_EOVERFLOW, "a cell holds more particles than the sort capacity");
+  if (st & ST_TIMEOUT)
+    return engine_fail(E, DPD_ETIMEOUT,
+                       "the cell scan's look-back gave up waiting for a tile (nothing was updated "
+                       "past it; reload the state)");
   if (st & ST_BAND)
     return engine_fail(E, DPD_EBAND,
                        "a drift exceeded the band margin; reduce dt or raise band_margin");

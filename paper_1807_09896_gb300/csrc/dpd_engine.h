@@ -38,6 +38,10 @@ struct Engine {
   StepParams graph_P = {};
   int graph_n = -1, graph_ncells = -1, graph_nsys = -1, graph_variant = -1, graph_len = -1;
   int use_graph = 1, graph_steps = 20, force_variant = 0;
+  int scan_stall_tile = -1;  // test hook of the cell scan (see launch_scan)
+  // host mirror of DevCounters::sums_pending: the last step enqueued ran a
+  // Newton's-third-law force kernel and left its sums for the next drift
+  bool sums_pending = false;
   uint64_t launches = 0;
   std::string* err = nullptr;  // where failure messages go
 };
@@ -56,8 +60,13 @@ void engine_enqueue_sort(Engine& E);
 // Pair force on arr[cur]; kick = 1 adds dt/2 F(t+dt), completing the closing kick whose
 // first half the drift kernel stored in vel.
 void engine_enqueue_force(Engine& E, int kick);
-// One full time step from arr[cur]; flips cur.
-void engine_enqueue_step(Engine& E);
+// One full time step from arr[cur]; flips cur.  With a Newton's-third-law force shape
+// the step leaves its force in the fixed-point sums for the next drift, unless
+// finish is set (then the finish pass completes the state, as the adjoint needs).
+void engine_enqueue_step(Engine& E, bool finish = false);
+// Complete a state left pending by a step (finish pass); a no-op otherwise.  Every
+// reader of the state between steps calls this first.
+void engine_settle(Engine& E);
 // nsteps steps, replayed from CUDA graphs where possible.  Does not wait.
 int engine_step(Engine& E, int nsteps);
 // nsteps steps launched one by one with events between phases; mean ms per phase.

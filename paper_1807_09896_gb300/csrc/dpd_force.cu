@@ -206,19 +206,19 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
 // (later in cell order), the next cell in x, and the rows (dy, dz) = (+1, 0),
 // (-1, +1), (0, +1), (+1, +1) of three cells each (13 of the 26 neighbour cells; at
 // least three cells per axis make every pair of cells meet once).  The pair force
-// f_ij goes to i and -f_ij (what j computes, bit for bit) to j.  Sums are kept in
-// 64-bit fixed point, 2^32 units per force unit, one array per component (the three
-// atomics of a pair then land in different L2 sectors): integer additions commute, so the
-// result does not depend on the order in which the atomics land and stays bitwise
-// reproducible.  Solid particles take part as the first particle of a pair (their
-// pairs with fluid particles in their half shell) but receive nothing.  A second
-// pass converts the sums, completes the closing kick and clears them.
+// f_ij goes to i and -f_ij (what j computes, bit for bit) to j.  The partners' shares
+// are summed in 64-bit fixed point, 2^32 units per force unit, one array per component
+// (the three atomics of a pair then land in different L2 sectors); i's own share, the
+// binary32 sum of the pairs it evaluated, goes to frc without an atomic and joins the
+// sums as one more integer term.  Integer additions commute, so the result does not
+// depend on the order in which the atomics land and stays bitwise reproducible.  Solid
+// particles take part as the first particle of a pair (their pairs with fluid
+// particles in their half shell) but receive nothing.  The next drift (or a finish
+// pass, where the state is read between steps) converts the sums, completes the
+// closing kick and clears them.
 // ---------------------------------------------------------------------------
-constexpr float kFixScale = 4294967296.0f;  // 2^32
-constexpr float kFixInvF = 1.0f / 4294967296.0f;  // 2^-32
-
 __device__ __forceinline__ void fix_add(unsigned long long* a, float v) {
-  atomicAdd(a, (unsigned long long)__float2ll_rn(v * kFixScale));
+  atomicAdd(a, (unsigned long long)to_fixed(v));
 }
 
 // forward rows of the half shell, r = 0..3: (dy, dz) = (+1, 0), (-1, +1), (0, +1), (+1, +1)
@@ -347,11 +347,9 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
     if (cnt < kListCap) break;  // the cells ran out before the list filled
     cnt = 0;
   }
-  if (!solid_i) {
-    fix_add(&facc[i], fx);
-    fix_add(&facc[stride + i], fy);
-    fix_add(&facc[2 * stride + i], fz);
-  }
+  // the own share goes to frc without an atomic (nothing else writes it): whoever reads
+  // the sums adds it as one more integer term
+  A.frc[i] = solid_i ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(fx, fy, fz, 0.f);
   // fixed point cannot carry a NaN or a force beyond its range: flag them here (every
   // pair this thread evaluated is in its own float sum)
   const float fmax = fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz)));
@@ -365,43 +363,44 @@ k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
            DevCounters* ctrs) {
   __shared__ int list[kListCap][kForceThreads];
   __shared__ uint32_t seg_b[5][kForceThreads], seg_e[5][kForceThreads];
+  // the forces stay in the sums: the next drift (or a finish pass) converts them
+  mark_sums_pending(ctrs, nsys, 1u);
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
   if (i >= n) return;
   const float4 pi = A.pos[i];
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
+    if (scan_failed(ctrs + sk)) return;
     force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, A,
                                                           facc, (size_t)n, i, pi, ctrs + sk, list,
                                                           seg_b, seg_e);
   } else {
+    if (scan_failed(ctrs)) return;
     force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, A, facc, (size_t)n, i, pi,
                                                           ctrs, list, seg_b, seg_e);
   }
 }
 
-// Second pass: the fixed-point sum becomes the force (one rounding from the exact
-// integer), the closing kick is completed and the sum cleared for the next step.
+// Finish pass: the fixed-point sums become the force, the closing kick is completed
+// and the sums cleared.  A time step leaves this to the next drift; the pass runs
+// when the state is read (or handed on) between steps, and after the initial force.
 template <bool kBatch>
 __global__ void __launch_bounds__(256) k_force_finish(StepParams P0, const SysDesc* __restrict__ S,
                                                       int nsys, Arrays A,
                                                       unsigned long long* __restrict__ facc, int n,
                                                       DevCounters* ctrs, int kick) {
+  mark_sums_pending(ctrs, nsys, 0u);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (is_solid(A.pos[i].w)) {  // nothing accumulates for solid particles
     A.frc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  unsigned long long* ax = facc + i;
-  unsigned long long* ay = ax + n;
-  unsigned long long* az = ay + n;
-  // one rounding from the exact integer; the power-of-two scale is exact
-  const float fx = __ll2float_rn((long long)*ax) * kFixInvF;
-  const float fy = __ll2float_rn((long long)*ay) * kFixInvF;
-  const float fz = __ll2float_rn((long long)*az) * kFixInvF;
-  *ax = 0ull;
-  *ay = 0ull;
-  *az = 0ull;
+  const float3 f = fixed_sum_force(facc, (size_t)n, (size_t)i, A.frc[i]);
+  const float fx = f.x, fy = f.y, fz = f.z;
+  facc[i] = 0ull;
+  facc[(size_t)n + i] = 0ull;
+  facc[2 * (size_t)n + i] = 0ull;
   const float4 vti = A.vt[i];
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
@@ -420,6 +419,7 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
         const uint32_t* __restrict__ start_all, int n, DevCounters* ctrs, int kick) {
   __shared__ int list[kListCap][kForceThreads];
   __shared__ uint32_t seg_b[9][kForceThreads], seg_e[9][kForceThreads];
+  mark_sums_pending(ctrs, nsys, 0u);  // this kernel completes the state itself
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
   if (i >= n) return;
   const float4 pi = A.pos[i];
@@ -429,9 +429,11 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   }
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
+    if (scan_failed(ctrs + sk)) return;
     force_body<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,
                                                        A, i, pi, list, seg_b, seg_e, kick);
   } else {
+    if (scan_failed(ctrs)) return;
     force_body<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, ctrs, A, i, pi, list, seg_b,
                                                        seg_e, kick);
   }
@@ -492,11 +494,6 @@ const char* force_variant_name(int v) {
   return (v >= 0 && v < force_variants()) ? names[v] : "?";
 }
 
-int force_variant_kernels(int variant) {
-  if (variant < 0 || variant >= force_variants()) variant = 0;
-  return kForceVariants[variant].n3 ? 2 : 1;
-}
-
 void launch_force_pairs(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
                         const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr,
                         int kick, int variant, cudaStream_t s) {
@@ -514,13 +511,15 @@ void launch_force_pairs(const StepParams& P0, const SysDesc* S, int nsys, const 
                                                                             n, ctr);
 }
 
-void launch_force_finish(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                         unsigned long long* facc, int n, DevCounters* ctr, int kick, int variant,
-                         cudaStream_t s) {
-  if (n <= 0) return;
+bool force_variant_newton3(int variant) {
   if (variant < 0 || variant >= force_variants()) variant = 0;
-  if (!kForceVariants[variant].n3) return;
-  const int nb2 = (n + 255) / 256;
+  return kForceVariants[variant].n3;
+}
+
+void launch_force_finish(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
+                         unsigned long long* facc, int n, DevCounters* ctr, int kick,
+                         cudaStream_t s) {
+  const int nb2 = n > 0 ? (n + 255) / 256 : 1;
   if (nsys == 1)
     k_force_finish<false><<<nb2, 256, 0, s>>>(P0, S, nsys, A, facc, n, ctr, kick);
   else
@@ -531,7 +530,7 @@ void launch_force(const StepParams& P0, const SysDesc* S, int nsys, const Arrays
                   const uint32_t* start, unsigned long long* facc, int n, DevCounters* ctr, int kick,
                   int variant, cudaStream_t s) {
   launch_force_pairs(P0, S, nsys, A, start, facc, n, ctr, kick, variant, s);
-  launch_force_finish(P0, S, nsys, A, facc, n, ctr, kick, variant, s);
+  if (force_variant_newton3(variant)) launch_force_finish(P0, S, nsys, A, facc, n, ctr, kick, s);
 }
 
 }  // namespace dpd

@@ -44,11 +44,30 @@ __device__ __forceinline__ float wrap_coord(float x, float L) {
 
 __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cell_off,
                                                DevCounters* ctr, const Arrays& A,
-                                               const CellList& C, int i) {
+                                               const CellList& C,
+                                               unsigned long long* __restrict__ facc, int n, int i) {
   float4 p = A.pos[i];
   if (!is_solid(p.w)) {
-    const float4 v = A.vel[i];
-    const float4 f = A.frc[i];
+    float4 v = A.vel[i];
+    float3 f;
+    if (ctr->sums_pending) {
+      // The last force kernel left the force in the fixed-point sums and v without the
+      // second half of its closing kick: convert the sums (and clear them for the next
+      // force), then complete the kick unless the particle was reflected (vel.w = 1).
+      // Same arithmetic as the finish pass, so the bits do not depend on which ran.
+      f = fixed_sum_force(facc, (size_t)n, (size_t)i, A.frc[i]);
+      facc[i] = 0ull;
+      facc[(size_t)n + i] = 0ull;
+      facc[2 * (size_t)n + i] = 0ull;
+      if (v.w == 0.0f) {
+        v.x = fmaf(P.half_dt, f.x + P.g[0], v.x);
+        v.y = fmaf(P.half_dt, f.y + P.g[1], v.y);
+        v.z = fmaf(P.half_dt, f.z + P.g[2], v.z);
+      }
+    } else {
+      const float4 f4 = A.frc[i];
+      f = make_float3(f4.x, f4.y, f4.z);
+    }
     const float Fx = f.x + P.g[0], Fy = f.y + P.g[1], Fz = f.z + P.g[2];
     const float dx = fmaf(P.half_dt2, Fx, P.dt * v.x);
     const float dy = fmaf(P.half_dt2, Fy, P.dt * v.y);
@@ -91,9 +110,9 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
           atomicAdd(&ctr->fallbacks, 1ull);
         }
         x = bx; y = by; z = bz;
-        const float4 vb = make_float4(2.0f * vw.x - v.x, 2.0f * vw.y - v.y, 2.0f * vw.z - v.z, 0.0f);
-        vh = vb;  // a reflected particle keeps its new velocity (no kick)
-        vt = make_float4(vb.x, vb.y, vb.z, 1.0f);
+        const float4 vb = make_float4(2.0f * vw.x - v.x, 2.0f * vw.y - v.y, 2.0f * vw.z - v.z, 1.0f);
+        vh = vb;  // a reflected particle keeps its new velocity (no kick); .w flags it
+        vt = vb;
         atomicAdd(&ctr->reflections, 1ull);
       }
     }
@@ -139,7 +158,8 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
 // faster on the 1M channel and 25% faster on a 64-system batch.
 template <bool kBatch>
 __global__ void __launch_bounds__(256, kBatch ? 6 : 8) k_integrate(StepParams P0, const SysDesc* __restrict__ S,
-                                                   int nsys, Arrays A, CellList C, int n,
+                                                   int nsys, Arrays A, CellList C,
+                                                   unsigned long long* __restrict__ facc, int n,
                                                    DevCounters* ctrs, int bump) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   // Thread k < nsys advances system k's noise counter for the force of this step;
@@ -148,9 +168,9 @@ __global__ void __launch_bounds__(256, kBatch ? 6 : 8) k_integrate(StepParams P0
   if (i >= n) return;
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
-    integrate_body(S[sk].P, S[sk].cell_off, ctrs + sk, A, C, i);
+    integrate_body(S[sk].P, S[sk].cell_off, ctrs + sk, A, C, facc, n, i);
   } else {
-    integrate_body(P0, 0u, ctrs, A, C, i);
+    integrate_body(P0, 0u, ctrs, A, C, facc, n, i);
   }
 }
 
@@ -166,15 +186,24 @@ __global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellLis
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of the per-cell counts: block sums, then the scan inside each
-// block with the block's offset.  For up to kScanFuseMax blocks each block sums
-// the totals before it itself; beyond that a one-block pass scans the totals in
-// between.  No block waits on another, so nothing can spin.  Warp scans use
-// __shfl_up_sync.  The last pass also zeroes the counts for the next step.
+// Exclusive scan of the per-cell counts in one pass (decoupled look-back, Merrill
+// and Garland 2016).  Blocks take tiles of kScanChunk cells in the order they start
+// (a ticket), so every tile's predecessors are running or done.  A tile publishes
+// its own total, looks back over its predecessors' published words (a warp reads 32
+// at a time) until it meets an inclusive prefix, publishes its own inclusive prefix
+// and writes its starts.  A published word is (epoch, flag, value) in 64 bits; the
+// epoch is the launch's ticket count / tiles, so words of an earlier launch read as
+// "not yet published" and nothing needs clearing between launches.  Every wait is
+// bounded: after kScanSpinLimit polls the tile sets ST_TIMEOUT in every system's
+// status and carries on with what it has; the kernels that index through the starts
+// check that bit first and do nothing, so a timed-out scan cannot drive them out of
+// range.  The scan also zeroes the counts for the next step.
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 256;
-constexpr int kScanPerThread = 8;
+constexpr int kScanThreads = 512;
+constexpr int kScanPerThread = 16;
 constexpr int kScanChunk = kScanThreads * kScanPerThread;
+constexpr int kScanSpinLimit = 4096;
+constexpr uint32_t kTileAggregate = 1u, kTilePrefix = 2u;
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const int lane = threadIdx.x & 31;
@@ -205,56 +234,88 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return base + inc - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* count, int m,
-                                                              uint32_t* blocksum) {
-  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPerThread;
-  uint32_t s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k)
-    if (base + k < m) s += count[base + k];
-  uint32_t tot;
-  block_excl_scan(s, &tot);
-  if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+__device__ __forceinline__ unsigned long long tile_word(uint32_t epoch, uint32_t flag, uint32_t v) {
+  return ((unsigned long long)((epoch << 2) | flag) << 32) | v;
 }
 
-// One block scans the block sums in place (exclusive), looping over chunks.
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* blocksum, int nb) {
-  uint32_t carry = 0;
-  for (int off = 0; off < nb; off += kScanThreads) {
-    const int j = off + threadIdx.x;
-    const uint32_t v = j < nb ? blocksum[j] : 0u;
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan(v, &tot);
-    if (j < nb) blocksum[j] = carry + ex;
-    carry += tot;
-  }
+__device__ __forceinline__ void publish(unsigned long long* w, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(w), "l"(v) : "memory");
 }
 
-// Few blocks: each block sums the totals of the blocks before it itself (at most
-// kScanFuseMax values), so no separate pass scans the totals.
-constexpr int kScanFuseMax = 1024;
+__device__ __forceinline__ unsigned long long peek(const unsigned long long* w) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+  return v;
+}
 
-template <bool kOwnOffset>
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* count, int m,
-                                                            const uint32_t* blocksum,
-                                                            uint32_t* start, uint32_t n_total) {
-  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPerThread;
+// stall_tile >= 0 (a test hook, set only through an option): that tile publishes
+// nothing, so its successors' look-back runs out and the launch reports ST_TIMEOUT.
+__global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t* count, int m, uint32_t* start,
+                                                       uint32_t n_total, unsigned long long* tiles,
+                                                       unsigned long long* ticket, int ntiles,
+                                                       DevCounters* ctrs, int nsys, int stall_tile) {
+  __shared__ unsigned long long s_ticket;
+  __shared__ uint32_t s_excl;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1ull);
+  __syncthreads();
+  const int t = (int)(s_ticket % (unsigned long long)ntiles);
+  const uint32_t epoch = (uint32_t)((s_ticket / (unsigned long long)ntiles + 1ull) & 0x3fffffffull);
+  const int base = t * kScanChunk + threadIdx.x * kScanPerThread;
   uint32_t v[kScanPerThread];
-  uint32_t s = 0;
+  uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanPerThread; ++k) {
     v[k] = (base + k < m) ? count[base + k] : 0u;
-    s += v[k];
+    sum += v[k];
   }
-  uint32_t tot, off;
-  if constexpr (kOwnOffset) {
-    uint32_t part = 0;
-    for (int j = threadIdx.x; j < (int)blockIdx.x; j += kScanThreads) part += blocksum[j];
-    block_excl_scan(part, &off);
-  } else {
-    off = blocksum[blockIdx.x];
+  uint32_t total;
+  const uint32_t local = block_excl_scan(sum, &total);
+  const bool stalled = t == stall_tile;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane == 0 && !stalled)
+      publish(&tiles[t], tile_word(epoch, t == 0 ? kTilePrefix : kTileAggregate, total));
+    uint32_t excl = 0;
+    bool timed_out = false;
+    int end = t - 1;  // the window is tiles end - 31 .. end, lane 0 the nearest
+    int polls = 0;
+    while (end >= 0) {
+      const int j = end - lane;
+      uint32_t flag = kTilePrefix, val = 0;  // before tile 0: an inclusive prefix of 0
+      if (j >= 0) {
+        const unsigned long long w = peek(&tiles[j]);
+        const uint32_t hi = (uint32_t)(w >> 32);
+        flag = (hi >> 2) == epoch ? (hi & 3u) : 0u;
+        val = (uint32_t)w;
+      }
+      const unsigned pmask = __ballot_sync(0xffffffffu, flag == kTilePrefix);
+      const unsigned xmask = __ballot_sync(0xffffffffu, flag == 0u);
+      const int first_p = pmask ? __ffs(pmask) - 1 : 32;
+      const unsigned before = first_p == 32 ? 0xffffffffu : ((1u << first_p) - 1u);
+      if (xmask & before) {  // a nearer predecessor has not published yet: wait
+        if (++polls > kScanSpinLimit) {
+          timed_out = true;
+          break;
+        }
+        __nanosleep(64);
+        continue;
+      }
+      uint32_t part = lane <= first_p ? val : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      excl += part;
+      if (first_p < 32) break;
+      end -= 32;
+    }
+    if (lane == 0) {
+      if (t > 0 && !stalled) publish(&tiles[t], tile_word(epoch, kTilePrefix, excl + total));
+      if (timed_out)
+        for (int k = 0; k < nsys; ++k) atomicOr(&ctrs[k].status, ST_TIMEOUT);
+      s_excl = excl;
+    }
   }
-  uint32_t run = off + block_excl_scan(s, &tot);
+  __syncthreads();
+  uint32_t run = s_excl + local;
 #pragma unroll
   for (int k = 0; k < kScanPerThread; ++k) {
     if (base + k < m) {
@@ -263,7 +324,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* count, int
     }
     run += v[k];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) start[m] = n_total;
+  if (t == ntiles - 1 && threadIdx.x == 0) start[m] = n_total;
 }
 
 // ---------------------------------------------------------------------------
@@ -288,10 +349,14 @@ __global__ void k_scatter(CellList C, int n, DevCounters* ctr) {
 // sum.  Sorting the indices themselves needs no other load.
 constexpr int kCellSortCap = 48;
 
-__global__ void k_cell_sort(CellList C, int ncells, DevCounters* ctr) {
+__global__ void k_cell_sort(CellList C, int ncells, int n, DevCounters* ctr) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
   const uint32_t b = C.start[c], e = C.start[c + 1];
+  if (b > e || e > (uint32_t)n) {  // starts not a valid prefix (only after a failed scan)
+    atomicOr(&ctr->status, ST_OVERFLOW);
+    return;
+  }
   const int m = (int)(e - b);
   if (m <= 1) return;
   if (m > kCellSortCap) {
@@ -455,6 +520,9 @@ __global__ void k_band(StepParams P, uint8_t* band) {
   band[c] = neg ? 1 : 0;
 }
 
+// Phase field below which a loaded fluid particle counts as inside the solid.
+constexpr float kLostPhi = 1e-4f;
+
 // Build the internal arrays from caller input (any order, id a permutation).
 __global__ void k_load(StepParams P, const float4* in_pos, const float4* in_vel, const int* in_id,
                        const uint8_t* in_type, Arrays A, uint32_t* seen, int n, DevCounters* ctr) {
@@ -479,7 +547,10 @@ __global__ void k_load(StepParams P, const float4* in_pos, const float4* in_vel,
     const float3 vw = wall_velocity(P, axis_coord(p, P.sh_axis));
     v = make_float4(vw.x, vw.y, vw.z, 0.0f);
   }
-  if (!solid && phi_at(P, p.x, p.y, p.z) < 0.0f) atomicOr(&ctr->status, ST_LOST);
+  // A step decides reflections on the exact drifted position and then stores it
+  // rounded to binary32, so a particle that ended just outside the wall can read a
+  // phase field a few 1e-6 below zero; only a particle clearly inside the solid is lost.
+  if (!solid && phi_at(P, p.x, p.y, p.z) < -kLostPhi) atomicOr(&ctr->status, ST_LOST);
   // stored at index id: the first cell order, and every later one, then does not
   // depend on the order of the input
   A.pos[id] = p;
@@ -526,14 +597,15 @@ static bool bump_folded(int n, int nsys) { return n > 0 && nsys <= n; }
 int integrate_kernels(int n, int nsys) { return (n > 0 ? 1 : 0) + (bump_folded(n, nsys) ? 0 : 1); }
 
 void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                      const CellList& C, int n, DevCounters* ctr, cudaStream_t s) {
+                      const CellList& C, unsigned long long* facc, int n, DevCounters* ctr,
+                      cudaStream_t s) {
   const int bump = bump_folded(n, nsys) ? 1 : 0;
   if (!bump) k_bump_step<<<blocks(nsys, 128), 128, 0, s>>>(ctr, nsys);
   if (n <= 0) return;
   if (nsys == 1)
-    k_integrate<false><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr, bump);
+    k_integrate<false><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
   else
-    k_integrate<true><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, n, ctr, bump);
+    k_integrate<true><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
 }
 
 void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
@@ -541,19 +613,15 @@ void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, 
   if (n > 0) k_key<<<blocks(n, 256), 256, 0, s>>>(S, nsys, A, C, n);
 }
 
-int scan_blocks(int ncells) { return blocks(ncells, kScanChunk); }
+int scan_blocks(int ncells) { return ncells > 0 ? blocks(ncells, kScanChunk) : 1; }
 
-int scan_kernels(int ncells) { return scan_blocks(ncells) <= kScanFuseMax ? 2 : 3; }
+int scan_kernels(int) { return 1; }
 
-void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s) {
-  const int nb = scan_blocks(ncells);
-  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum);
-  if (nb <= kScanFuseMax) {
-    k_scan_down<true><<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum, C.start, (uint32_t)n);
-  } else {
-    k_scan_top<<<1, kScanThreads, 0, s>>>(C.blocksum, nb);
-    k_scan_down<false><<<nb, kScanThreads, 0, s>>>(C.count, ncells, C.blocksum, C.start, (uint32_t)n);
-  }
+void launch_scan(const CellList& C, int ncells, int n, DevCounters* ctr, int nsys, int stall_tile,
+                 cudaStream_t s) {
+  const int nt = scan_blocks(ncells);
+  k_scan<<<nt, kScanThreads, 0, s>>>(C.count, ncells, C.start, (uint32_t)n, C.tile, C.ticket, nt, ctr,
+                                     nsys, stall_tile);
 }
 
 void launch_scatter(const CellList& C, int n, DevCounters* ctr, cudaStream_t s) {
@@ -561,7 +629,7 @@ void launch_scatter(const CellList& C, int n, DevCounters* ctr, cudaStream_t s) 
 }
 
 void launch_cell_sort(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s) {
-  if (n > 0) k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, ncells, ctr);
+  if (n > 0) k_cell_sort<<<blocks(ncells, 128), 128, 0, s>>>(C, ncells, n, ctr);
 }
 
 void launch_gather(const CellList& C, const Arrays& src, const Arrays& dst, int n, cudaStream_t s) {

@@ -38,6 +38,8 @@ _SIGS = {
     "dpd_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
     "dpd_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "dpd_adjoint_window": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, _vp, _i, _vp, _vp]),
+    "dpd_adjoint_window_record": (_i, [_vp, _i, _i, _i, _d, _d, _i, _d, _vp, _i, _vp, _vp, _vp, _vp,
+                                       _vp, _vp, _vp]),
     "dpd_velocity_profile": (_i, [_vp, _i, _i, _d, _d, _vp, _i]),
     "dpd_velocity_profile_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _vp, _i, _vp]),
     "dpd_relax_phase_field": (_i, [_vp, _vp, _d, _d, _i, _d, _i, _vp]),
@@ -181,6 +183,27 @@ def dpd_adjoint_window(h, nsteps, ckpt_every, axis, wall_lo, wall_hi, target, bi
                                                 float(bin_width), _ptr(t), int(bool(tie_sigma)),
                                                 _ptr(loss), _ptr(grad)))
     return float(loss[0]), grad
+
+
+def dpd_adjoint_window_record(h, nsteps, ckpt_every, axis, wall_lo, wall_hi, target, bin_width,
+                              tie_sigma=True):
+    """As dpd_adjoint_window, plus the record of include/dpd.h: a dict with ckpt and
+    adj ((nseg + 1, n, 3, 4) float32, id order), seg_grad (nseg, 3), coef (nbins,)
+    and seg_step (nseg + 1,)."""
+    t = np.ascontiguousarray(target, np.float64)
+    n = dpd_num_particles(h)[0]
+    nseg = int(nsteps) // int(ckpt_every)
+    rec = {"ckpt": np.zeros((nseg + 1, n, 3, 4), np.float32),
+           "adj": np.zeros((nseg + 1, n, 3, 4), np.float32),
+           "seg_grad": np.zeros((nseg, 3), np.float64), "coef": np.zeros(len(t), np.float32),
+           "seg_step": np.zeros(nseg + 1, np.uint32)}
+    grad = np.zeros(3, np.float64)
+    loss = np.zeros(1, np.float64)
+    _check(h, load_library().dpd_adjoint_window_record(
+        h, int(nsteps), int(ckpt_every), int(axis), float(wall_lo), float(wall_hi), len(t),
+        float(bin_width), _ptr(t), int(bool(tie_sigma)), _ptr(loss), _ptr(grad), _ptr(rec["ckpt"]),
+        _ptr(rec["adj"]), _ptr(rec["seg_grad"]), _ptr(rec["coef"]), _ptr(rec["seg_step"])))
+    return float(loss[0]), grad, rec
 
 
 def dpd_num_particles(h):

@@ -186,6 +186,19 @@ def _sphere_distance(pts, cs, rs, L):
     return d
 
 
+def _sphere_distance_two(pts, cs, rs, L):
+    """Signed distances to the nearest and the second-nearest sphere surface."""
+    d1 = np.full(len(pts), np.inf)
+    d2 = np.full(len(pts), np.inf)
+    for c, r in zip(cs, rs):
+        dd = pts - c
+        dd -= L * np.round(dd / L)
+        e = np.sqrt((dd * dd).sum(axis=1)) - r
+        d2 = np.minimum(d2, np.maximum(d1, e))
+        d1 = np.minimum(d1, e)
+    return d1, d2
+
+
 # Beyond this distance from every surface tanh(d / (sqrt(2) eps)) rounds to 1 in binary32.
 _PHI_SATURATION_DISTANCE = 7.0
 
@@ -228,14 +241,18 @@ def sphere_pack(L: float, nspheres: int, rmin: float, rmax: float, rho: float = 
     ncand = int(round(rho * L ** 3))
     cand = rng.uniform(0, L, size=(ncand, 3))
     d = np.empty(ncand)
+    d2 = np.empty(ncand)
     chunk = 1 << 18
     for s in range(0, ncand, chunk):
-        d[s:s + chunk] = _sphere_distance(cand[s:s + chunk], cs, rs, L)
+        d[s:s + chunk], d2[s:s + chunk] = _sphere_distance_two(cand[s:s + chunk], cs, rs, L)
     # A thin shell 0 < d <= 0.02 r_c next to the curved surfaces stays empty: there the
     # grid-interpolated phase field can fall a little below zero (interpolation error
     # ~ h^2/8 |phi''| ~ 0.012 in phi, ~ 0.009 r_c in distance), and a fluid particle
-    # must start on the fluid side of the sharp interface.
-    fpos = cand[d > 0.02]
+    # must start on the fluid side of the sharp interface.  Where two surfaces come
+    # within ~1 r_c of each other the distance to their union has a ridge, and a grid
+    # cell across the ridge interpolates up to ~h/2 below it: points there within
+    # 0.15 r_c of a surface stay empty too.
+    fpos = cand[(d > 0.02) & ~((d < 0.15) & (d2 < 1.0))]
     spos = cand[(d <= 0) & (d >= -layer)]
     return _finish(f"spheres_{L:g}_{nspheres}", box, phi, h, fpos, spos, kBT, rng)
 

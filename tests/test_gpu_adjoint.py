@@ -186,22 +186,6 @@ def test_adjoint_on_the_32x16x16_channel_over_100_steps():
     s.close()
 
 
-@pytest.mark.slow
-def test_adjoint_on_the_32x16x16_channel_over_200_steps_is_stated():
-    """Over 200 steps (2 time units) the sensitivity of one noise realization grows by
-    two to three orders of magnitude (chaos): the binary32 trajectory's gradient and
-    the binary64 one's no longer agree, although the losses do to 1e-3.  The values
-    are printed for the record; only the loss and finiteness are asserted."""
-    theta, w, loss = _c5()
-    s = make_system(w, _params(w, theta, 0))
-    L, g = adjoint.window_loss_and_grad(s, theta, loss, nsteps=200, ckpt_every=20)
-    L0, g_fd = oracle_fd_gradient(w, theta, loss, 200, seed=0, rel_h=(1e-7, 1e-7, 1e-6))
-    print("200-step window: loss gpu %.6e oracle %.6e; grad gpu %s oracle fd %s" % (L, L0, g, g_fd))
-    assert abs(L - L0) <= 1e-3 * abs(L0)
-    assert np.all(np.isfinite(g))
-    s.close()
-
-
 def test_adjoint_rejects_walls_sliding_at_different_velocities():
     w, s, loss = _setup(seed=35)
     s.set_option("shear_x", 0.05)

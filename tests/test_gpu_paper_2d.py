@@ -11,17 +11,27 @@ The paper does not state dt or lambda, and its frozen wall particles come from a
 equilibrated fluid; over four seeds the values here differ from the printed ones by
 2-4% at kBT = 1 (seed spread 2%) and by 0.1-2% at kBT = 0.1 (spread 0.5%).  The bounds
 below leave room for one run's statistical error on top.
+
+FP32 against FP64: the binary64 oracle ran each seed's run from the same start on the
+same schedule (tests/golden/make_fp64_observables.py); the trajectories separate
+(chaos), so the binary32 and binary64 observables must agree within their combined
+statistical errors (jackknife over the 6 sampling blocks, 4 sigma).
 """
 import os
 
 import numpy as np
 import pytest
 
+from flow_analysis import jackknife
 from paper_1807_09896_gb300 import dpd, inputs
 
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_poiseuille_2d.txt")
+# binary64 oracle runs of the same starts, seeds and schedules (make_fp64_observables.py)
+FP64 = os.path.join(os.path.dirname(__file__), "golden", "fp64_observables.npz")
+SEEDS = (0, 1)
+BLOCKS = 6
 
 
 def _rows():
@@ -44,7 +54,13 @@ def _built():
     _build.build()
 
 
-def _poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess, W=10.0, Lx=30.0, g=0.02, rho=4.0):
+W2D, G2D, RHO2D, NB2D = 10.0, 0.02, 4.0, 100
+
+
+def _poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess, Lx=30.0):
+    """Block profiles (6 blocks of 100 time units, sampled every 10 steps, 100 bins
+    across the channel) after 300 time units from the parabola of mu_guess."""
+    W, g, rho = W2D, G2D, RHO2D
     w = inputs.channel_2d(Lx, W, kBT=kBT, seed=seed)
     assert w.n == 1440
     y = w.pos[:, 1].astype(np.float64)
@@ -53,17 +69,24 @@ def _poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess, W=10.0, Lx=30.0, g=
     s = dpd.System.from_workload(w, a_ff=a, a_fs=a, gamma=gamma, sigma=sigma, kBT=kBT, dt=dt,
                                  g=(g, 0.0, 0.0), rho=rho, seed=seed)
     s.step(int(300.0 / dt))
-    nb = 100
-    s.profile(1, nb, 0.0, W, mode=3)
     s.set_option("sample_every", 10)
-    s.step(int(600.0 / dt))
-    prof = s.profile(1, nb, 0.0, W, mode=2)
+    blocks = []
+    for _ in range(BLOCKS):
+        s.profile(1, NB2D, 0.0, W, mode=3)
+        s.step(int(100.0 / dt))
+        blocks.append(s.profile(1, NB2D, 0.0, W, mode=2).copy())
     pos = s.state()[0]
     s.close()
     assert np.all(pos[:, 2] == np.float32(1.5))  # the layer stays exactly planar
+    return np.array(blocks)
+
+
+def eq19_observables(prof):
+    """mu from the fitted maximum and from the mean velocity (Eq. 19), and Re."""
+    W, g, rho = W2D, G2D, RHO2D
     cnt = prof[:, 0]
     u = prof[:, 1] / cnt
-    yc = (np.arange(nb) + 0.5) * W / nb
+    yc = (np.arange(NB2D) + 0.5) * W / NB2D
     inner = (yc > 1.0) & (yc < W - 1.0)
     c2, c1, c0 = np.polyfit(yc[inner], u[inner], 2)
     vmax = c0 - c1 * c1 / (4 * c2)
@@ -71,7 +94,11 @@ def _poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess, W=10.0, Lx=30.0, g=
     half = W / 2
     mu_max = rho * g * half * half / (2 * vmax)  # Eq. 19, first form
     mu_bar = rho * g * half * half / (3 * vbar)  # Eq. 19, second form
-    return mu_max, mu_bar, rho * vbar * W / mu_max
+    return np.array([mu_max, mu_bar, rho * vbar * W / mu_max])
+
+
+def _with_errors(blocks):
+    return jackknife(lambda keep: eq19_observables(blocks[keep].sum(axis=0)), len(blocks))
 
 
 @pytest.mark.slow
@@ -79,9 +106,19 @@ def _poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess, W=10.0, Lx=30.0, g=
 def test_printed_viscosity_and_reynolds_number(row):
     kBT, a, gamma, sigma, mu_max_p, mu_bar_p, re_p = row
     dt = 0.01 if kBT >= 1.0 else 0.005  # gamma = 45 needs the smaller step
-    runs = np.array([_poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess=mu_bar_p)
-                     for seed in (0, 1)])
-    mu_max, mu_bar, re = runs.mean(axis=0)
+    fp64 = np.load(FP64)
+    runs, errs = [], []
+    for seed in SEEDS:
+        blocks = _poiseuille_2d(kBT, a, gamma, sigma, dt, seed, mu_guess=mu_bar_p)
+        (obs, err) = _with_errors(blocks)
+        # the binary64 oracle from the same start, seed and schedule
+        (obs64, err64) = _with_errors(fp64[f"poiseuille2d_kBT{kBT:g}_seed{seed}"])
+        print(f"kBT {kBT} seed {seed}: (mu(vmax), mu(vbar), Re) binary32 {obs} +- {err}, "
+              f"binary64 {obs64} +- {err64}")
+        assert np.all(np.abs(obs - obs64) <= 4 * np.hypot(err, err64))
+        runs.append(obs)
+        errs.append(err)
+    mu_max, mu_bar, re = np.mean(runs, axis=0)
     print(f"kBT {kBT}: mu(vmax) {mu_max:.4f} (paper {mu_max_p}), mu(vbar) {mu_bar:.4f} "
           f"(paper {mu_bar_p}), Re {re:.2f} (paper {re_p})")
     tol = 0.08 if kBT >= 1.0 else 0.04

@@ -13,9 +13,12 @@ Measured (one seed, 5 x 10^5 steps of 0.005): eps 0.05 -> 0.784 (Eq. 20: 0.808),
 eps 0.1 -> 0.550 (0.507), eps 0.2 -> 0.285 (0.248), eps 0.3 -> 0.165 (0.140); the
 paper finds agreement at small eps and fits its own data over all eps by Eq. 21
 (0.840, 0.564, 0.332, 0.217 at the same eps).  The test holds the two smallest
-fractions to 12% of Eq. 20 and checks the decrease with eps.
+fractions to 12% of Eq. 20 and checks the decrease with eps.  FP32 against FP64: the
+binary64 oracle ran the same runs (tests/golden/make_fp64_observables.py); the two
+means must agree within 4 combined standard errors.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -23,6 +26,8 @@ import pytest
 from paper_1807_09896_gb300 import dpd, inputs
 
 pytestmark = pytest.mark.gpu
+
+FP64 = os.path.join(os.path.dirname(__file__), "golden", "fp64_observables.npz")
 
 
 def eq20(eps):
@@ -63,15 +68,27 @@ def _normalised_mean_velocity(eps, L=28.0, mu=3.41, g=0.005, rho=4.0, kBT=0.1, s
     pos = s.state()[0]
     s.close()
     assert np.all(pos[:, 2] == np.float32(1.5))
-    return 4 * math.pi * float(np.mean(vs)) * mu / (rho * g * L * L)
+    return _normalise(np.asarray(vs), L, mu, g, rho)
+
+
+def _normalise(vs, L=28.0, mu=3.41, g=0.005, rho=4.0):
+    """Normalised mean velocity of the samples and its standard error (the samples
+    are 50 time units apart, longer than the flow's relaxation time L^2 / (4 pi^2 nu))."""
+    f = 4 * math.pi * mu / (rho * g * L * L)
+    return f * float(np.mean(vs)), f * float(np.std(vs, ddof=1)) / math.sqrt(len(vs))
 
 
 @pytest.mark.slow
 def test_mean_velocity_through_a_cylinder_array_follows_eq20_at_small_fraction():
+    fp64 = np.load(FP64)
     out = {}
     for eps in (0.05, 0.1, 0.2):
-        out[eps] = _normalised_mean_velocity(eps)
-        print(f"eps {eps}: {out[eps]:.4f}  Eq. 20 {eq20(eps):.4f}  Eq. 21 {eq21(eps):.4f}")
+        out[eps], err = _normalised_mean_velocity(eps)
+        # binary64 oracle, same start, seed and schedule (make_fp64_observables.py)
+        v64, err64 = _normalise(fp64[f"cylinders_eps{eps:g}"])
+        print(f"eps {eps}: {out[eps]:.4f} +- {err:.4f} (binary64 {v64:.4f} +- {err64:.4f})  "
+              f"Eq. 20 {eq20(eps):.4f}  Eq. 21 {eq21(eps):.4f}")
+        assert abs(out[eps] - v64) <= 4 * math.hypot(err, err64)
     for eps in (0.05, 0.1):
         assert abs(out[eps] / eq20(eps) - 1.0) < 0.12
     assert out[0.05] > out[0.1] > out[0.2] > 0
