@@ -258,7 +258,7 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
  * enqueued by stepping calls so far), "kernels_per_step", "force_variants",
  * "force_newton3" (1 if the current shape evaluates each pair once), "scan_tiles"
- * (tiles of 8192 cells in the cell scan). */
+ * (tiles of 2048 cells in the cell scan). */
 int dpd_set_option(dpd_t* h, const char* key, double value);
 int dpd_get_option(dpd_t* h, const char* key, double* value);
 

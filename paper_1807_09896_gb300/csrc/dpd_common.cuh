@@ -8,7 +8,8 @@
 //   frc  {fx, fy, fz, 0}  pair force f(t) (body force not included)
 // Between the steps of a Newton's-third-law force shape the force is not in frc but
 // in 64-bit fixed-point sums, and vel still lacks the second half of the closing
-// kick; DevCounters::sums_pending says so (see the drift kernel).
+// kick; the host knows which state it left and launches the drift kernel that
+// completes it (see the drift kernel).
 #pragma once
 
 #include <cstdint>
@@ -34,11 +35,6 @@ struct DevCounters {
   uint32_t step;                 // noise counter of the most recent force evaluation
   unsigned long long reflections;
   unsigned long long fallbacks;
-  // 1 while the force of the current state is still in the fixed-point pair sums
-  // and the second half of its closing kick has not been applied (the state a
-  // Newton's-third-law force kernel leaves); the next drift completes both
-  uint32_t sums_pending;
-  uint32_t pad;
 };
 
 // True when a timed-out cell scan left the cell starts unusable: kernels that index
@@ -60,21 +56,15 @@ __device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v 
 // The force of particle i: its partners' fixed-point sums plus its own share, one
 // rounding from the exact integer (the power-of-two scale is exact).  Integer sums
 // do not depend on the order of their terms, so neither does the result.
-__device__ __forceinline__ float3 fixed_sum_force(const unsigned long long* facc, size_t n, size_t i,
-                                                  float4 own) {
-  const long long x = (long long)facc[i] + to_fixed(own.x);
-  const long long y = (long long)facc[n + i] + to_fixed(own.y);
-  const long long z = (long long)facc[2 * n + i] + to_fixed(own.z);
+__device__ __forceinline__ float3 fixed_sum_force(unsigned long long sx, unsigned long long sy,
+                                                  unsigned long long sz, float4 own) {
+  const long long x = (long long)sx + to_fixed(own.x);
+  const long long y = (long long)sy + to_fixed(own.y);
+  const long long z = (long long)sz + to_fixed(own.z);
   return make_float3(__ll2float_rn(x) * kFixInvF, __ll2float_rn(y) * kFixInvF,
                      __ll2float_rn(z) * kFixInvF);
 }
 
-// Mark systems 0..nsys-1 as holding (1) or not holding (0) pending sums; grid-stride,
-// so that every system is marked whatever the launch size.
-__device__ __forceinline__ void mark_sums_pending(DevCounters* ctrs, int nsys, uint32_t v) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsys; k += gridDim.x * blockDim.x)
-    ctrs[k].sums_pending = v;
-}
 
 // Everything a step kernel needs, passed by value.
 struct StepParams {

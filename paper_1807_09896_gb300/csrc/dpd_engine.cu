@@ -34,10 +34,11 @@ static cudaError_t dev_alloc(T** p, size_t count) {
 }
 
 void engine_free_graphs(Engine& E) {
-  for (auto& g : E.graph) {
-    if (g) cudaGraphExecDestroy(g);
-    g = nullptr;
-  }
+  for (auto& row : E.graph)
+    for (auto& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
 }
 
 static void free_particle_buffers(Engine& E) {
@@ -175,7 +176,8 @@ void engine_settle(Engine& E) {
 static void enqueue_step_from(Engine& E, int c, bool finish) {
   const Arrays& A = E.arr[c];
   const Arrays& B = E.arr[c ^ 1];
-  launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.n, E.d_ctr, E.stream);
+  launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.sums_pending, E.n, E.d_ctr,
+                   E.stream);
   launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
   launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
   launch_force_pairs(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
@@ -194,24 +196,35 @@ void engine_enqueue_step(Engine& E, bool finish) {
   E.launches += engine_kernels_per_step(E);
 }
 
-static int build_graph(Engine& E, int c) {
+// Capture graph_steps steps from arr[c], entered with the sums in mode m.
+static int build_graph(Engine& E, int c, int m) {
   cudaGraph_t g = nullptr;
+  const bool entry = E.sums_pending;
   ECU(E, cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal));
   int cc = c;
   for (int k = 0; k < E.graph_steps; ++k) {
     enqueue_step_from(E, cc, false);
     cc ^= 1;
   }
+  E.graph_exit_pending[c][m] = E.sums_pending;
+  E.sums_pending = entry;  // nothing ran yet: the replay below moves the state on
   cudaError_t e = cudaStreamEndCapture(E.stream, &g);
   if (e != cudaSuccess)
     return engine_fail(E, DPD_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&E.graph[c], g, 0);
+  e = cudaGraphInstantiate(&E.graph[c][m], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    E.graph[c] = nullptr;
+    E.graph[c][m] = nullptr;
     return engine_fail(E, DPD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
   }
   return DPD_OK;
+}
+
+static bool any_graph(const Engine& E) {
+  for (const auto& row : E.graph)
+    for (const auto g : row)
+      if (g) return true;
+  return false;
 }
 
 // True if the captured graphs were built for the engine as it is now.
@@ -222,12 +235,13 @@ static bool graph_key_matches(const Engine& E) {
 }
 
 int engine_step(Engine& E, int nsteps) {
-  if ((E.graph[0] || E.graph[1]) && !graph_key_matches(E)) engine_free_graphs(E);
+  if (any_graph(E) && !graph_key_matches(E)) engine_free_graphs(E);
   int left = nsteps;
   while (left > 0) {
     if (E.use_graph && left >= E.graph_steps) {
-      if (!E.graph[E.cur]) {
-        const int rc = build_graph(E, E.cur);
+      const int m = E.sums_pending ? 1 : 0;
+      if (!E.graph[E.cur][m]) {
+        const int rc = build_graph(E, E.cur, m);
         if (rc) return rc;
         memcpy(&E.graph_P, &E.h_sys[0].P, sizeof(StepParams));
         E.graph_n = E.n;
@@ -236,7 +250,8 @@ int engine_step(Engine& E, int nsteps) {
         E.graph_variant = E.force_variant;
         E.graph_len = E.graph_steps;
       }
-      ECU(E, cudaGraphLaunch(E.graph[E.cur], E.stream));
+      ECU(E, cudaGraphLaunch(E.graph[E.cur][m], E.stream));
+      E.sums_pending = E.graph_exit_pending[E.cur][m];
       // graph_steps is even: the state ends in the buffers it started in
       E.launches += (uint64_t)engine_kernels_per_step(E) * E.graph_steps;
       left -= E.graph_steps;
@@ -258,7 +273,8 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
     const Arrays& A = E.arr[E.cur];
     const Arrays& B = E.arr[E.cur ^ 1];
     cudaEventRecord(ev[0], E.stream);
-    launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.n, E.d_ctr, E.stream);
+    launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.sums_pending, E.n, E.d_ctr,
+                     E.stream);
     cudaEventRecord(ev[1], E.stream);
     launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
     cudaEventRecord(ev[2], E.stream);
@@ -370,15 +386,17 @@ int engine_read_counters(Engine& E, uint32_t* status) {
 
 int engine_status_code(Engine& E, uint32_t st) {
   if (st == 0) return DPD_OK;
+  // a timed-out scan leaves invalid cell starts, whose consequences (an overflow, a lost
+  // or non-finite particle) it would otherwise hide behind: it goes first
+  if (st & ST_TIMEOUT)
+    return engine_fail(E, DPD_ETIMEOUT,
+                       "the cell scan's look-back gave up waiting for a tile (nothing was updated "
+                       "past it; reload the state)");
   if (st & ST_NAN) return engine_fail(E, DPD_ENAN, "non-finite position, velocity or force");
   if (st & ST_LOST) return engine_fail(E, DPD_ELOST, "a fluid particle is at phi < 0");
   if (st & ST_BADID) return engine_fail(E, DPD_EINVAL, "ids are not a permutation of 0..n-1");
   if (st & ST_OVERFLOW)
     return engine_fail(E, DPD_EOVERFLOW, "a cell holds more particles than the sort capacity");
-  if (st & ST_TIMEOUT)
-    return engine_fail(E, DPD_ETIMEOUT,
-                       "the cell scan's look-back gave up waiting for a tile (nothing was updated "
-                       "past it; reload the state)");
   if (st & ST_BAND)
     return engine_fail(E, DPD_EBAND,
                        "a drift exceeded the band margin; reduce dt or raise band_margin");

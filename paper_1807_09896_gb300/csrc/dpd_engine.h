@@ -32,15 +32,18 @@ struct Engine {
   // fixed-point pair-force sums of the Newton's-third-law force shapes: 3 per
   // particle, zero between steps (the finish kernel clears what it reads)
   unsigned long long* facc = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // step graphs by the buffers the state starts in and by whether its sums are pending
+  // when the graph starts (its first drift differs); exit_pending: the mode it leaves
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool graph_exit_pending[2][2] = {{false, false}, {false, false}};
   // what the graphs were captured with (system 0's parameters travel by value in
   // the kernel arguments; sizes set the grids): a replay with anything else rebuilds
   StepParams graph_P = {};
   int graph_n = -1, graph_ncells = -1, graph_nsys = -1, graph_variant = -1, graph_len = -1;
   int use_graph = 1, graph_steps = 20, force_variant = 0;
   int scan_stall_tile = -1;  // test hook of the cell scan (see launch_scan)
-  // host mirror of DevCounters::sums_pending: the last step enqueued ran a
-  // Newton's-third-law force kernel and left its sums for the next drift
+  // the last step enqueued ran a Newton's-third-law force kernel and left its force in
+  // the fixed-point sums for the next drift (which then runs in its pending form)
   bool sums_pending = false;
   uint64_t launches = 0;
   std::string* err = nullptr;  // where failure messages go

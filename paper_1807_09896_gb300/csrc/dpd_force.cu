@@ -363,8 +363,6 @@ k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
            DevCounters* ctrs) {
   __shared__ int list[kListCap][kForceThreads];
   __shared__ uint32_t seg_b[5][kForceThreads], seg_e[5][kForceThreads];
-  // the forces stay in the sums: the next drift (or a finish pass) converts them
-  mark_sums_pending(ctrs, nsys, 1u);
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
   if (i >= n) return;
   const float4 pi = A.pos[i];
@@ -389,14 +387,14 @@ __global__ void __launch_bounds__(256) k_force_finish(StepParams P0, const SysDe
                                                       int nsys, Arrays A,
                                                       unsigned long long* __restrict__ facc, int n,
                                                       DevCounters* ctrs, int kick) {
-  mark_sums_pending(ctrs, nsys, 0u);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (is_solid(A.pos[i].w)) {  // nothing accumulates for solid particles
     A.frc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  const float3 f = fixed_sum_force(facc, (size_t)n, (size_t)i, A.frc[i]);
+  const size_t ns = (size_t)n;
+  const float3 f = fixed_sum_force(facc[i], facc[ns + i], facc[2 * ns + i], A.frc[i]);
   const float fx = f.x, fy = f.y, fz = f.z;
   facc[i] = 0ull;
   facc[(size_t)n + i] = 0ull;
@@ -419,7 +417,6 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
         const uint32_t* __restrict__ start_all, int n, DevCounters* ctrs, int kick) {
   __shared__ int list[kListCap][kForceThreads];
   __shared__ uint32_t seg_b[9][kForceThreads], seg_e[9][kForceThreads];
-  mark_sums_pending(ctrs, nsys, 0u);  // this kernel completes the state itself
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
   if (i >= n) return;
   const float4 pi = A.pos[i];
@@ -519,7 +516,8 @@ bool force_variant_newton3(int variant) {
 void launch_force_finish(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
                          unsigned long long* facc, int n, DevCounters* ctr, int kick,
                          cudaStream_t s) {
-  const int nb2 = n > 0 ? (n + 255) / 256 : 1;
+  if (n <= 0) return;
+  const int nb2 = (n + 255) / 256;
   if (nsys == 1)
     k_force_finish<false><<<nb2, 256, 0, s>>>(P0, S, nsys, A, facc, n, ctr, kick);
   else

@@ -42,20 +42,32 @@ __device__ __forceinline__ float wrap_coord(float x, float L) {
   return x;
 }
 
+template <bool kPending>
 __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cell_off,
                                                DevCounters* ctr, const Arrays& A,
                                                const CellList& C,
                                                unsigned long long* __restrict__ facc, int n, int i) {
+  // every load of the particle up front, before any branch on them: the kernel is
+  // bound by memory latency, and a load behind a branch on another load would wait
+  // for two round trips (solid particles read a little they do not need)
   float4 p = A.pos[i];
+  float4 v = A.vel[i];
+  const float4 f4 = A.frc[i];
+  unsigned long long sx = 0ull, sy = 0ull, sz = 0ull;
+  if constexpr (kPending) {
+    sx = facc[i];
+    sy = facc[(size_t)n + i];
+    sz = facc[2 * (size_t)n + i];
+  }
   if (!is_solid(p.w)) {
-    float4 v = A.vel[i];
     float3 f;
-    if (ctr->sums_pending) {
-      // The last force kernel left the force in the fixed-point sums and v without the
-      // second half of its closing kick: convert the sums (and clear them for the next
-      // force), then complete the kick unless the particle was reflected (vel.w = 1).
-      // Same arithmetic as the finish pass, so the bits do not depend on which ran.
-      f = fixed_sum_force(facc, (size_t)n, (size_t)i, A.frc[i]);
+    if constexpr (kPending) {
+      // The last force kernel left the force in the fixed-point sums (f4 holds the
+      // particle's own share) and v without the second half of its closing kick:
+      // convert the sums (and clear them for the next force), then complete the kick
+      // unless the particle was reflected (vel.w = 1).  Same arithmetic as the finish
+      // pass, so the bits do not depend on which ran.
+      f = fixed_sum_force(sx, sy, sz, f4);
       facc[i] = 0ull;
       facc[(size_t)n + i] = 0ull;
       facc[2 * (size_t)n + i] = 0ull;
@@ -65,7 +77,6 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
         v.z = fmaf(P.half_dt, f.z + P.g[2], v.z);
       }
     } else {
-      const float4 f4 = A.frc[i];
       f = make_float3(f4.x, f4.y, f4.z);
     }
     const float Fx = f.x + P.g[0], Fy = f.y + P.g[1], Fz = f.z + P.g[2];
@@ -155,9 +166,12 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
 // Latency-bound (three particle loads, then mostly arithmetic): the register cap lets 8
 // blocks (6 for the batch form) share an SM, which hides more load latency.  The values
 // it spills belong to the rare reflection branch; measured with the same bits 13%
-// faster on the 1M channel and 25% faster on a 64-system batch.
-template <bool kBatch>
-__global__ void __launch_bounds__(256, kBatch ? 6 : 8) k_integrate(StepParams P0, const SysDesc* __restrict__ S,
+// faster on the 1M channel and 25% faster on a 64-system batch.  The pending form holds
+// three more loads in flight and gets the 6-block cap (40 registers).
+// kPending: the state was left by a Newton's-third-law force kernel (its force in the
+// fixed-point sums, its closing kick half done); the host knows which and chooses.
+template <bool kBatch, bool kPending>
+__global__ void __launch_bounds__(256, kBatch || kPending ? 6 : 8) k_integrate(StepParams P0, const SysDesc* __restrict__ S,
                                                    int nsys, Arrays A, CellList C,
                                                    unsigned long long* __restrict__ facc, int n,
                                                    DevCounters* ctrs, int bump) {
@@ -168,9 +182,9 @@ __global__ void __launch_bounds__(256, kBatch ? 6 : 8) k_integrate(StepParams P0
   if (i >= n) return;
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
-    integrate_body(S[sk].P, S[sk].cell_off, ctrs + sk, A, C, facc, n, i);
+    integrate_body<kPending>(S[sk].P, S[sk].cell_off, ctrs + sk, A, C, facc, n, i);
   } else {
-    integrate_body(P0, 0u, ctrs, A, C, facc, n, i);
+    integrate_body<kPending>(P0, 0u, ctrs, A, C, facc, n, i);
   }
 }
 
@@ -199,8 +213,8 @@ __global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellLis
 // check that bit first and do nothing, so a timed-out scan cannot drive them out of
 // range.  The scan also zeroes the counts for the next step.
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 512;
-constexpr int kScanPerThread = 16;
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
 constexpr int kScanChunk = kScanThreads * kScanPerThread;
 constexpr int kScanSpinLimit = 4096;
 constexpr uint32_t kTileAggregate = 1u, kTilePrefix = 2u;
@@ -597,15 +611,23 @@ static bool bump_folded(int n, int nsys) { return n > 0 && nsys <= n; }
 int integrate_kernels(int n, int nsys) { return (n > 0 ? 1 : 0) + (bump_folded(n, nsys) ? 0 : 1); }
 
 void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                      const CellList& C, unsigned long long* facc, int n, DevCounters* ctr,
-                      cudaStream_t s) {
+                      const CellList& C, unsigned long long* facc, bool pending, int n,
+                      DevCounters* ctr, cudaStream_t s) {
   const int bump = bump_folded(n, nsys) ? 1 : 0;
   if (!bump) k_bump_step<<<blocks(nsys, 128), 128, 0, s>>>(ctr, nsys);
   if (n <= 0) return;
-  if (nsys == 1)
-    k_integrate<false><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
-  else
-    k_integrate<true><<<blocks(n, 256), 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
+  const int nb = blocks(n, 256);
+  if (nsys == 1) {
+    if (pending)
+      k_integrate<false, true><<<nb, 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
+    else
+      k_integrate<false, false><<<nb, 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
+  } else {
+    if (pending)
+      k_integrate<true, true><<<nb, 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
+    else
+      k_integrate<true, false><<<nb, 256, 0, s>>>(P0, S, nsys, A, C, facc, n, ctr, bump);
+  }
 }
 
 void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,

@@ -8,10 +8,11 @@ namespace dpd {
 // Drift, reflection and cell key of every particle, after advancing each system's
 // noise counter (inside the drift launch when nsys <= n, else by a launch of its own).
 // P0: parameters of system 0, used directly when nsys == 1.
-// facc: the fixed-point pair sums, read (and cleared) by systems whose sums are pending.
+// pending: the state was left by a Newton's-third-law force kernel, its force still in
+// the fixed-point sums facc, which the drift converts (and clears) first.
 void launch_integrate(const StepParams& P0, const SysDesc* S, int nsys, const Arrays& A,
-                      const CellList& C, unsigned long long* facc, int n, DevCounters* ctr,
-                      cudaStream_t s);
+                      const CellList& C, unsigned long long* facc, bool pending, int n,
+                      DevCounters* ctr, cudaStream_t s);
 void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, int n,
                 cudaStream_t s);
 // Kernels one launch_integrate enqueues.

@@ -27,7 +27,7 @@ def _built():
 
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_a_stalled_scan_tile_times_out_and_the_system_recovers(use_graph):
-    w = inputs.channel(48.0, 24.0, 14.0, seed=41)  # 48 x 24 x 16 cells: 3 tiles of 8192
+    w = inputs.channel(24.0, 16.0, 14.0, seed=41)  # 24 x 16 x 16 cells: 3 tiles of 2048
     p = params_for(w, g=(0.02, 0.0, 0.0), seed=3)
     s = make_system(w, p, use_graph=use_graph, graph_steps=4)
     ref = make_system(w, p, use_graph=use_graph, graph_steps=4)
