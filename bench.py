@@ -87,7 +87,7 @@ def _args():
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint and precision lines")
     ap.add_argument("--force-variant", type=int, default=-1,
                     help="use this pair-force launch shape instead of tuning (e.g. to profile it)")
-    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the extra workload lines (channel_200k, spheres_c3)")
     ap.add_argument("--timed-ms", type=float, default=1500.0,
