@@ -251,10 +251,11 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * parameters), "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
  * default 20), "force_variant" (launch shape of the pair-force kernel, see
- * dpd_autotune), "scan_stall_tile" (a test hook, default -1: tile k >= 0 of the
- * single-pass cell scan publishes nothing, so the tiles after it give up waiting
- * and the step returns DPD_ETIMEOUT; the force kernels skip that step and the state stays
- * invalid until the next dpd_set_particles).
+ * dpd_autotune), "adjoint_tape_mb" (see dpd_adjoint_window), "scan_stall_tile" (a
+ * test hook, default -1: tile k >= 0 of the single-pass cell scan publishes
+ * nothing, so the tiles after it give up waiting and the step returns
+ * DPD_ETIMEOUT; the force kernels skip that step and the state stays invalid
+ * until the next dpd_set_particles).
  * Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
  * enqueued by stepping calls so far), "kernels_per_step", "force_variants",
  * "force_newton3" (1 if the current shape evaluates each pair once), "scan_tiles"
@@ -287,9 +288,12 @@ int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
  * d/dgamma includes the random force (DPD_EINVAL unless kBT > 0 and gamma > 0);
  * 0 runs with sigma as set and holds it fixed.  grad[3] receives
  * dL/da_fs, dL/dgamma, dL/dg_x; loss_out (may be NULL) receives L.
- * Memory: a checkpoint every ckpt_every steps (nsteps must be a multiple) and a
- * record of ckpt_every steps; the backward pass recomputes one segment at a
- * time.  Requires reflect_variant 0, force_law 0 and walls moving together
+ * Memory: the reverse pass walks a record of every step (the state, 64 B per
+ * particle, and the step's sort permutation and cell starts).  If the whole
+ * window's record fits the budget of option "adjoint_tape_mb" (MiB, default 2048)
+ * the forward pass keeps it; otherwise it keeps a checkpoint every ckpt_every steps
+ * (nsteps must be a multiple in either case) and the reverse pass recomputes one
+ * segment at a time into a record of ckpt_every steps.  Both give the same bits.  Requires reflect_variant 0, force_law 0 and walls moving together
  * (shear 0); otherwise DPD_EINVAL. */
 int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
                        double wall_hi, int nbins, double bin_width, const double* target,

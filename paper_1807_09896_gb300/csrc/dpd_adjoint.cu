@@ -137,85 +137,108 @@ __device__ __forceinline__ float phi_and_grad(const StepParams& P, float x, floa
 // Parameter adjoints sum over ordered pairs with target i: d f_ij / d a_fs = w e
 // (fluid-solid pairs), d f_ij / d gamma = -w^2 eu e + (kBT / sigma) w xi / sqrt(dt) e
 // when sigma = sqrt(2 gamma kBT) is tied to gamma (Eq. 8).
+// Four lanes per target: lane dz + 1 walks the nine neighbour cells of plane dz
+// (dz = -1, 0, 1; the fourth lane idles), and the lanes' sums are combined with two
+// shuffles.  The calibration windows are small (tens of thousands of particles), where
+// one thread per target left ~5 warps per SM and the kernel waited on its loads.
+constexpr int kAdjLanes = 4;
+
 __global__ void __launch_bounds__(128)
 k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restrict__ vt,
             const uint32_t* __restrict__ start, int n, uint32_t step, const float4* __restrict__ rbar,
             const float4* __restrict__ vbar, const float4* __restrict__ fbar, float4* Rb, float4* Vb,
             float tie_coef, double* theta, const DevCounters* ctr) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / kAdjLanes, sub = t % kAdjLanes;
   double ta = 0.0, tg = 0.0;
+  float Rx = 0.f, Ry = 0.f, Rz = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
+  bool target = false;
   // cell starts left by a timed-out scan are not a valid prefix (the status reports it)
   if (i < n && !scan_failed(ctr)) {
     const float4 pi = pos[i];
-    if (is_solid(pi.w)) {
-      Rb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      Vb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
+    target = !is_solid(pi.w);
+    if (target && sub < 3) {
       const float4 vti = vt[i];
       const uint32_t idi = id_of(pi.w);
       const float4 fbi = fbar[i], vbi = vbar[i];
       const float kick_i = vti.w == 0.0f ? P.half_dt : 0.0f;
       const float Fx = fbi.x + kick_i * vbi.x, Fy = fbi.y + kick_i * vbi.y, Fz = fbi.z + kick_i * vbi.z;
-      const float4 rbi = rbar[i];
-      float Rx = rbi.x, Ry = rbi.y, Rz = rbi.z, Ux = 0.f, Uy = 0.f, Uz = 0.f;
+      if (sub == 1) {  // the target's own rbar, once
+        const float4 rbi = rbar[i];
+        Rx = rbi.x;
+        Ry = rbi.y;
+        Rz = rbi.z;
+      }
       const int cx = cell_coord(pi.x, P.inv_edge[0], P.nc[0]);
       const int cy = cell_coord(pi.y, P.inv_edge[1], P.nc[1]);
       const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int x = wrap_node(cx + dx, P.nc[0]), y = wrap_node(cy + dy, P.nc[1]),
-                      z = wrap_node(cz + dz, P.nc[2]);
-            const int c = (z * P.nc[1] + y) * P.nc[0] + x;
-            for (uint32_t j = start[c]; j < start[c + 1]; ++j) {
-              const float4 pj = pos[j];
-              const float ddx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
-              const float ddy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
-              const float ddz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-              const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-              if (!(r2 < 1.0f && r2 > 0.0f)) continue;
-              const float inv_r = rsqrtf(r2);
-              const float r = r2 * inv_r;
-              const float w = 1.0f - r;
-              const float ex = ddx * inv_r, ey = ddy * inv_r, ez = ddz * inv_r;
-              const bool solid_j = is_solid(pj.w);
-              float ujx, ujy, ujz, a, Gx = Fx, Gy = Fy, Gz = Fz;
-              if (solid_j) {
-                ujx = P.vw[0]; ujy = P.vw[1]; ujz = P.vw[2];
-                a = P.a_fs;
-              } else {
-                const float4 vtj = vt[j];
-                ujx = vtj.x; ujy = vtj.y; ujz = vtj.z;
-                a = P.a_ff;
-                const float4 fbj = fbar[j], vbj = vbar[j];
-                const float kick_j = vtj.w == 0.0f ? P.half_dt : 0.0f;
-                Gx -= fbj.x + kick_j * vbj.x;
-                Gy -= fbj.y + kick_j * vbj.y;
-                Gz -= fbj.z + kick_j * vbj.z;
-              }
-              const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
-              const float eu = ex * ux + ey * uy + ez * uz;
-              const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.seed_lo, P.seed_hi);
-              const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
-              const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
-              const float eG = ex * Gx + ey * Gy + ez * Gz;
-              const float gw2 = P.gamma * w * w;
-              const float cu = -gw2 * eG * inv_r;
-              const float cm = m * inv_r;
-              Rx += m_r * eG * ex + cu * (ux - eu * ex) + cm * (Gx - eG * ex);
-              Ry += m_r * eG * ey + cu * (uy - eu * ey) + cm * (Gy - eG * ey);
-              Rz += m_r * eG * ez + cu * (uz - eu * ez) + cm * (Gz - eG * ez);
-              Ux -= gw2 * eG * ex;
-              Uy -= gw2 * eG * ey;
-              Uz -= gw2 * eG * ez;
-              const float eF = ex * Fx + ey * Fy + ez * Fz;
-              if (solid_j) ta += (double)(w * eF);
-              tg += (double)((-w * w * eu + tie_coef * w * xi) * eF);
+      const int dz = sub - 1;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x = wrap_node(cx + dx, P.nc[0]), y = wrap_node(cy + dy, P.nc[1]),
+                    z = wrap_node(cz + dz, P.nc[2]);
+          const int c = (z * P.nc[1] + y) * P.nc[0] + x;
+          for (uint32_t j = start[c]; j < start[c + 1]; ++j) {
+            const float4 pj = pos[j];
+            const float ddx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
+            const float ddy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
+            const float ddz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            if (!(r2 < 1.0f && r2 > 0.0f)) continue;
+            const float inv_r = rsqrtf(r2);
+            const float r = r2 * inv_r;
+            const float w = 1.0f - r;
+            const float ex = ddx * inv_r, ey = ddy * inv_r, ez = ddz * inv_r;
+            const bool solid_j = is_solid(pj.w);
+            float ujx, ujy, ujz, a, Gx = Fx, Gy = Fy, Gz = Fz;
+            if (solid_j) {
+              ujx = P.vw[0]; ujy = P.vw[1]; ujz = P.vw[2];
+              a = P.a_fs;
+            } else {
+              const float4 vtj = vt[j];
+              ujx = vtj.x; ujy = vtj.y; ujz = vtj.z;
+              a = P.a_ff;
+              const float4 fbj = fbar[j], vbj = vbar[j];
+              const float kick_j = vtj.w == 0.0f ? P.half_dt : 0.0f;
+              Gx -= fbj.x + kick_j * vbj.x;
+              Gy -= fbj.y + kick_j * vbj.y;
+              Gz -= fbj.z + kick_j * vbj.z;
             }
+            const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
+            const float eu = ex * ux + ey * uy + ez * uz;
+            const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.seed_lo, P.seed_hi);
+            const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
+            const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
+            const float eG = ex * Gx + ey * Gy + ez * Gz;
+            const float gw2 = P.gamma * w * w;
+            const float cu = -gw2 * eG * inv_r;
+            const float cm = m * inv_r;
+            Rx += m_r * eG * ex + cu * (ux - eu * ex) + cm * (Gx - eG * ex);
+            Ry += m_r * eG * ey + cu * (uy - eu * ey) + cm * (Gy - eG * ey);
+            Rz += m_r * eG * ez + cu * (uz - eu * ez) + cm * (Gz - eG * ez);
+            Ux -= gw2 * eG * ex;
+            Uy -= gw2 * eG * ey;
+            Uz -= gw2 * eG * ez;
+            const float eF = ex * Fx + ey * Fy + ez * Fz;
+            if (solid_j) ta += (double)(w * eF);
+            tg += (double)((-w * w * eu + tie_coef * w * xi) * eF);
           }
-      Rb[i] = make_float4(Rx, Ry, Rz, 0.f);
-      Vb[i] = make_float4(Ux, Uy, Uz, 0.f);
+        }
     }
+  }
+  // the target's four lanes are adjacent: add their sums (every lane takes part)
+#pragma unroll
+  for (int o = 1; o < kAdjLanes; o <<= 1) {
+    Rx += __shfl_xor_sync(0xffffffffu, Rx, o);
+    Ry += __shfl_xor_sync(0xffffffffu, Ry, o);
+    Rz += __shfl_xor_sync(0xffffffffu, Rz, o);
+    Ux += __shfl_xor_sync(0xffffffffu, Ux, o);
+    Uy += __shfl_xor_sync(0xffffffffu, Uy, o);
+    Uz += __shfl_xor_sync(0xffffffffu, Uz, o);
+  }
+  if (i < n && sub == 0 && !scan_failed(ctr)) {
+    Rb[i] = target ? make_float4(Rx, Ry, Rz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    Vb[i] = target ? make_float4(Ux, Uy, Uz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   ta = warp_sum_d(ta);
   tg = warp_sum_d(tg);
@@ -326,6 +349,24 @@ __global__ void k_unsort3(const float4* __restrict__ key_pos, const float4* __re
   out[3 * (size_t)id + 2] = c[i];
 }
 
+// The record of one step in one launch: the four state arrays, the sort permutation
+// and the cell starts, copied to the step's slot of the record.
+__global__ void k_record(Arrays src, Arrays dst, const uint32_t* __restrict__ perm,
+                         uint32_t* __restrict__ perm_dst, const uint32_t* __restrict__ start,
+                         uint32_t* __restrict__ start_dst, int n, int nstart) {
+  const int m = n > nstart ? n : nstart;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+    if (q < n) {
+      dst.pos[q] = src.pos[q];
+      dst.vt[q] = src.vt[q];
+      dst.vel[q] = src.vel[q];
+      dst.frc[q] = src.frc[q];
+      perm_dst[q] = perm[q];
+    }
+    if (q < nstart) start_dst[q] = start[q];
+  }
+}
+
 struct Buf {
   std::vector<void*> ptrs;
   ~Buf() {
@@ -425,25 +466,40 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   B.nbins = nbins;
 
   Buf buf;
-  // checkpoints: the four state arrays of each segment start, plus the final state
-  std::vector<Arrays> ck(nseg + 1);
-  for (auto& A : ck) {
-    ACU(buf.alloc(&A.pos, n));
-    ACU(buf.alloc(&A.vt, n));
-    ACU(buf.alloc(&A.vel, n));
-    ACU(buf.alloc(&A.frc, n));
-  }
-  std::vector<Arrays> tape(K + 1);
-  std::vector<uint32_t*> tperm(K), tstart(K);
+  // The record of the steps the reverse pass walks: every state (four arrays), and every
+  // step's sort permutation and cell starts.  When the whole window's record fits the
+  // budget (option "adjoint_tape_mb") the forward pass keeps it and nothing is recomputed;
+  // otherwise the forward pass keeps a checkpoint every K steps and the reverse pass
+  // recomputes one segment at a time into a record of K steps.  Both give the same bits.
+  const size_t state_bytes = 4 * nf4;
+  const size_t step_bytes = sizeof(uint32_t) * ((size_t)n + (size_t)E.ncells + 1);
+  const bool whole = (double)((size_t)(nsteps + 1) * state_bytes + (size_t)nsteps * step_bytes) <=
+                     h->adjoint_tape_mb * 1048576.0;
+  const int T = whole ? nsteps : K;
+  std::vector<Arrays> tape(T + 1);
+  std::vector<uint32_t*> tperm(T), tstart(T);
   for (auto& A : tape) {
     ACU(buf.alloc(&A.pos, n));
     ACU(buf.alloc(&A.vt, n));
     ACU(buf.alloc(&A.vel, n));
     ACU(buf.alloc(&A.frc, n));
   }
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < T; ++k) {
     ACU(buf.alloc(&tperm[k], n));
     ACU(buf.alloc(&tstart[k], (size_t)E.ncells + 1));
+  }
+  // checkpoints: the four state arrays of each segment start, plus the final state
+  std::vector<Arrays> ck(nseg + 1);
+  for (int q2 = 0; q2 <= nseg; ++q2) {
+    if (whole) {
+      ck[q2] = tape[q2 * K];
+      continue;
+    }
+    Arrays& A = ck[q2];
+    ACU(buf.alloc(&A.pos, n));
+    ACU(buf.alloc(&A.vt, n));
+    ACU(buf.alloc(&A.vel, n));
+    ACU(buf.alloc(&A.frc, n));
   }
   float4 *rb[2], *vb[2], *fb[2], *Rb, *Vb, *zero4;
   for (int q = 0; q < 2; ++q) {
@@ -491,7 +547,13 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
     engine_enqueue_step(E, true);
     const Arrays& A = E.arr[E.cur];
     k_wall_profile<<<nblk(n, 256), 256, 0, st>>>(A.pos, A.vel, n, B, acc);
-    if (s % K == 0) ACU(copy_state(ck[s / K], A));
+    if (whole) {  // the record of step s (ck[] points into it)
+      const int m = n > E.ncells + 1 ? n : E.ncells + 1;
+      k_record<<<nblk(m, 256), 256, 0, st>>>(A, tape[s], E.cl.perm, tperm[s - 1], E.cl.start,
+                                             tstart[s - 1], n, E.ncells + 1);
+    } else if (s % K == 0) {
+      ACU(copy_state(ck[s / K], A));
+    }
   }
   ACU(cudaGetLastError());
   ACU(cudaMemcpyAsync(start_end, E.cl.start, start_bytes, cudaMemcpyDeviceToDevice, st));
@@ -544,29 +606,32 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
       ACU(cudaMemcpyAsync(rec->adj + (size_t)(seg + 1) * rec_floats, stage, sizeof(float) * rec_floats,
                           cudaMemcpyDeviceToHost, st));
     }
-    // recompute the segment, recording every step
-    ACU(copy_state(E.arr[E.cur], ck[seg]));
     const uint32_t seg_step = step0 + (uint32_t)(seg * K);
-    ACU(cudaMemcpyAsync(&E.d_ctr[0].step, &seg_step, sizeof seg_step, cudaMemcpyHostToDevice, st));
-    ACU(copy_state(tape[0], ck[seg]));
-    for (int k = 0; k < K; ++k) {
-      engine_enqueue_step(E, true);
-      ACU(copy_state(tape[k + 1], E.arr[E.cur]));
-      ACU(cudaMemcpyAsync(tperm[k], E.cl.perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
-      ACU(cudaMemcpyAsync(tstart[k], E.cl.start, sizeof(uint32_t) * ((size_t)E.ncells + 1),
-                          cudaMemcpyDeviceToDevice, st));
+    const int base = whole ? seg * K : 0;  // the segment's first step in the record
+    if (!whole) {
+      // recompute the segment, recording every step
+      ACU(copy_state(E.arr[E.cur], ck[seg]));
+      ACU(cudaMemcpyAsync(&E.d_ctr[0].step, &seg_step, sizeof seg_step, cudaMemcpyHostToDevice, st));
+      ACU(copy_state(tape[0], ck[seg]));
+      for (int k = 0; k < K; ++k) {
+        engine_enqueue_step(E, true);
+        const int m = n > E.ncells + 1 ? n : E.ncells + 1;
+        k_record<<<nblk(m, 256), 256, 0, st>>>(E.arr[E.cur], tape[k + 1], E.cl.perm, tperm[k],
+                                               E.cl.start, tstart[k], n, E.ncells + 1);
+      }
     }
     // reverse through the recorded steps
     for (int k = K - 1; k >= 0; --k) {
       const uint32_t step_new = seg_step + (uint32_t)k + 1;
-      const Arrays& An = tape[k + 1];
-      const Arrays& Ao = tape[k];
-      k_adj_force<<<nblk(n, 128), 128, 0, st>>>(P, An.pos, An.vt, tstart[k], n, step_new, rb[q], vb[q],
-                                                fb[q], Rb, Vb, tie, theta, E.d_ctr);
+      const Arrays& An = tape[base + k + 1];
+      const Arrays& Ao = tape[base + k];
+      k_adj_force<<<nblk((long)n * kAdjLanes, 128), 128, 0, st>>>(P, An.pos, An.vt, tstart[base + k], n, step_new, rb[q],
+                                                vb[q], fb[q], Rb, Vb, tie, theta, E.d_ctr);
       const int s_old = seg * K + k;  // global index of the previous state
-      k_adj_integrate<<<nblk(n, 256), 256, 0, st>>>(P, Ao.pos, Ao.vel, Ao.frc, An.pos, An.vt, tperm[k], n,
-                                                    Rb, Vb, vb[q], rb[q ^ 1], vb[q ^ 1], fb[q ^ 1], B,
-                                                    s_old >= 1 ? coef : nullptr, theta);
+      k_adj_integrate<<<nblk(n, 256), 256, 0, st>>>(P, Ao.pos, Ao.vel, Ao.frc, An.pos, An.vt,
+                                                    tperm[base + k], n, Rb, Vb, vb[q], rb[q ^ 1],
+                                                    vb[q ^ 1], fb[q ^ 1], B, s_old >= 1 ? coef : nullptr,
+                                                    theta);
       q ^= 1;
     }
     if (rec && rec->seg_grad && seg > 0) {
@@ -581,7 +646,7 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   // f(0) = f(r0, v0): its parameter dependence, with F-bar = fbar(0) (no kick)
   {
     const Arrays& A0 = ck[0];
-    k_adj_force<<<nblk(n, 128), 128, 0, st>>>(P, A0.pos, A0.vt, start0, n, step0, zero4, zero4,
+    k_adj_force<<<nblk((long)n * kAdjLanes, 128), 128, 0, st>>>(P, A0.pos, A0.vt, start0, n, step0, zero4, zero4,
                                               fb[q], Rb, Vb, tie, theta, E.d_ctr);
   }
   ACU(cudaGetLastError());

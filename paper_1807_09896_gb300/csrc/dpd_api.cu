@@ -544,6 +544,9 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     if (v < 2 || v > 1000 || v != std::floor(v) || ((int)v & 1))
       return fail(h, DPD_EINVAL, "graph_steps must be an even number in [2, 1000]");
     E.graph_steps = (int)v;
+  } else if (k == "adjoint_tape_mb") {
+    if (!(v >= 0.0)) return fail(h, DPD_EINVAL, "adjoint_tape_mb must be >= 0");
+    h->adjoint_tape_mb = v;
   } else if (k == "scan_stall_tile") {
     if (v < -1 || v != std::floor(v) || v > 1e9)
       return fail(h, DPD_EINVAL, "scan_stall_tile must be -1 or a tile index");
@@ -591,6 +594,7 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "force_variants") *v = dpd::force_variants();
   else if (k == "force_newton3") *v = dpd::force_variant_newton3(E.force_variant);
   else if (k == "scan_stall_tile") *v = E.scan_stall_tile;
+  else if (k == "adjoint_tape_mb") *v = h->adjoint_tape_mb;
   else if (k == "scan_tiles") *v = dpd::scan_blocks(h->ncells);
   else return fail(h, DPD_EINVAL, "unknown option '%s'", key);
   return DPD_OK;

@@ -31,6 +31,7 @@ struct dpd_system {
   uint64_t seed = 0;
   uint32_t sys = 0;
   int reflect_variant = 0;
+  double adjoint_tape_mb = 2048.0;  // budget for keeping a whole adjoint window's record
   int sample_every = 0;
   int nc[3] = {0, 0, 0};
   int ncells = 0;
