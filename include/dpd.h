@@ -293,8 +293,15 @@ int dpd_num_particles(dpd_t* h, int* n, int* n_fluid);
  * window's record fits the budget of option "adjoint_tape_mb" (MiB, default 2048)
  * the forward pass keeps it; otherwise it keeps a checkpoint every ckpt_every steps
  * (nsteps must be a multiple in either case) and the reverse pass recomputes one
- * segment at a time into a record of ckpt_every steps.  Both give the same bits.  Requires reflect_variant 0, force_law 0 and walls moving together
- * (shear 0); otherwise DPD_EINVAL. */
+ * segment at a time into a record of ckpt_every steps.  Both give the same bits.
+ * The device workspace (record, checkpoints, adjoint arrays) is kept by the system
+ * for the next window, grown when a window needs more, and freed by dpd_destroy or
+ * by setting "adjoint_tape_mb".
+ * Determinism: the loss bins are summed with integer atomics (velocity sums in
+ * units of 2^-24, |sum| < 2^39 per bin) and the parameter sums in per-warp slots
+ * added in a fixed order, so repeated calls on the same state give the same bits.
+ * Requires reflect_variant 0, force_law 0 and walls moving together (shear 0);
+ * otherwise DPD_EINVAL. */
 int dpd_adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double wall_lo,
                        double wall_hi, int nbins, double bin_width, const double* target,
                        int tie_sigma, double* loss_out, double grad[3]);

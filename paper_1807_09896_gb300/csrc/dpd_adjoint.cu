@@ -50,9 +50,14 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Forward loss statistics: per bin {count, sum vx} over fluid particles.
+// Fixed-point scale of the loss bins' velocity sums (|sum| < 2^39 per bin).  Integer
+// atomics make the sums, and the loss, independent of the order the warps add in.
+constexpr double kBinFix = 16777216.0;  // 2^24
+
+// Forward loss statistics: per bin {count, sum vx} over fluid particles, as integers
+// (the sum in units of 2^-24).
 __global__ void __launch_bounds__(256) k_wall_profile(const float4* pos, const float4* vel, int n,
-                                                      WallBins B, double* acc) {
+                                                      WallBins B, unsigned long long* acc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   bool pending = false;
@@ -73,11 +78,11 @@ __global__ void __launch_bounds__(256) k_wall_profile(const float4* pos, const f
     const int leader = __ffs(mask) - 1;
     const int b0 = __shfl_sync(0xffffffffu, bin, leader);
     const bool mine = pending && bin == b0;
-    const double c = warp_sum_d(mine ? 1.0 : 0.0);
+    const unsigned c = __popc(__ballot_sync(0xffffffffu, mine));
     const double s = warp_sum_d(mine ? vx : 0.0);
     if (lane == leader) {
-      atomicAdd(acc + 2 * b0, c);
-      atomicAdd(acc + 2 * b0 + 1, s);
+      atomicAdd(acc + 2 * b0, (unsigned long long)c);
+      atomicAdd(acc + 2 * b0 + 1, (unsigned long long)__double2ll_rn(s * kBinFix));
     }
     if (mine) pending = false;
     mask = __ballot_sync(0xffffffffu, pending);
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(128)
 k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restrict__ vt,
             const uint32_t* __restrict__ start, int n, uint32_t step, const float4* __restrict__ rbar,
             const float4* __restrict__ vbar, const float4* __restrict__ fbar, float4* Rb, float4* Vb,
-            float tie_coef, double* theta, const DevCounters* ctr) {
+            float tie_coef, double* tpart, const DevCounters* ctr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / kAdjLanes, sub = t % kAdjLanes;
   double ta = 0.0, tg = 0.0;
@@ -240,11 +245,14 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
     Rb[i] = target ? make_float4(Rx, Ry, Rz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     Vb[i] = target ? make_float4(Ux, Uy, Uz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  // each warp adds to its own slot (launches on one stream follow one another, so no
+  // two writers meet); k_theta_sum adds the slots in a fixed order
   ta = warp_sum_d(ta);
   tg = warp_sum_d(tg);
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(theta + 0, ta);
-    atomicAdd(theta + 1, tg);
+    const int w = t >> 5;
+    tpart[2 * w] += ta;
+    tpart[2 * w + 1] += tg;
   }
 }
 
@@ -257,7 +265,7 @@ k_adj_integrate(StepParams P, const float4* __restrict__ pos_old, const float4* 
                 const float4* __restrict__ vt_new, const uint32_t* __restrict__ perm, int n,
                 const float4* __restrict__ Rb, const float4* __restrict__ Vb,
                 const float4* __restrict__ vbar_new, float4* rbar_old, float4* vbar_old,
-                float4* fbar_old, WallBins B, const float* __restrict__ seed_coef, double* theta) {
+                float4* fbar_old, WallBins B, const float* __restrict__ seed_coef, double* tpart) {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   double tgx = 0.0;
   if (d < n) {
@@ -319,7 +327,33 @@ k_adj_integrate(StepParams P, const float4* __restrict__ pos_old, const float4* 
     fbar_old[o] = fb;
   }
   tgx = warp_sum_d(tgx);
-  if ((threadIdx.x & 31) == 0) atomicAdd(theta + 2, tgx);
+  if ((threadIdx.x & 31) == 0) tpart[d >> 5] += tgx;
+}
+
+// theta = (sum of the a_fs and gamma slots of k_adj_force, sum of the g_x slots of
+// k_adj_integrate), added in a fixed order: the gradient has the same bits from run to
+// run.  One block of kThetaThreads threads.
+constexpr int kThetaThreads = 256;
+__global__ void __launch_bounds__(kThetaThreads)
+k_theta_sum(const double* __restrict__ tpart_f, int nw_f, const double* __restrict__ tpart_i,
+            int nw_i, double* out) {
+  __shared__ double sh[3][kThetaThreads];
+  double a = 0.0, g = 0.0, x = 0.0;
+  for (int w = threadIdx.x; w < nw_f; w += kThetaThreads) {
+    a += tpart_f[2 * w];
+    g += tpart_f[2 * w + 1];
+  }
+  for (int w = threadIdx.x; w < nw_i; w += kThetaThreads) x += tpart_i[w];
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = g;
+  sh[2][threadIdx.x] = x;
+  __syncthreads();
+  for (int o = kThetaThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // Loss seed at the window's last state (same order as the state).
@@ -367,16 +401,15 @@ __global__ void k_record(Arrays src, Arrays dst, const uint32_t* __restrict__ pe
   }
 }
 
-struct Buf {
-  std::vector<void*> ptrs;
-  ~Buf() {
-    for (void* p : ptrs) cudaFree(p);
-  }
+// Carves the adjoint's arrays out of one workspace, each on a 256-byte boundary.  With
+// no base it only adds up the bytes (the sizing pass).
+struct Carve {
+  char* base = nullptr;
+  size_t off = 0;
   template <typename T>
-  cudaError_t alloc(T** p, size_t count) {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
-    if (e == cudaSuccess) ptrs.push_back(*p);
-    return e;
+  void alloc(T** p, size_t count) {
+    *p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (sizeof(T) * (count > 0 ? count : 1) + 255) & ~(size_t)255;
   }
 };
 
@@ -465,7 +498,6 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   B.inv_width = (float)(1.0 / bin_width);
   B.nbins = nbins;
 
-  Buf buf;
   // The record of the steps the reverse pass walks: every state (four arrays), and every
   // step's sort permutation and cell starts.  When the whole window's record fits the
   // budget (option "adjoint_tape_mb") the forward pass keeps it and nothing is recomputed;
@@ -478,47 +510,71 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   const int T = whole ? nsteps : K;
   std::vector<Arrays> tape(T + 1);
   std::vector<uint32_t*> tperm(T), tstart(T);
-  for (auto& A : tape) {
-    ACU(buf.alloc(&A.pos, n));
-    ACU(buf.alloc(&A.vt, n));
-    ACU(buf.alloc(&A.vel, n));
-    ACU(buf.alloc(&A.frc, n));
-  }
-  for (int k = 0; k < T; ++k) {
-    ACU(buf.alloc(&tperm[k], n));
-    ACU(buf.alloc(&tstart[k], (size_t)E.ncells + 1));
-  }
   // checkpoints: the four state arrays of each segment start, plus the final state
   std::vector<Arrays> ck(nseg + 1);
-  for (int q2 = 0; q2 <= nseg; ++q2) {
-    if (whole) {
-      ck[q2] = tape[q2 * K];
-      continue;
-    }
-    Arrays& A = ck[q2];
-    ACU(buf.alloc(&A.pos, n));
-    ACU(buf.alloc(&A.vt, n));
-    ACU(buf.alloc(&A.vel, n));
-    ACU(buf.alloc(&A.frc, n));
-  }
   float4 *rb[2], *vb[2], *fb[2], *Rb, *Vb, *zero4;
-  for (int q = 0; q < 2; ++q) {
-    ACU(buf.alloc(&rb[q], n));
-    ACU(buf.alloc(&vb[q], n));
-    ACU(buf.alloc(&fb[q], n));
-  }
-  ACU(buf.alloc(&Rb, n));
-  ACU(buf.alloc(&Vb, n));
-  ACU(buf.alloc(&zero4, n));
-  double *acc, *theta;
+  unsigned long long* acc;
+  // per-warp parameter sums of k_adj_force (two each) and k_adj_integrate (one each), and
+  // theta after the reversal of each segment (index seg; index 0 after the window start)
+  const int nw_f = nblk((long)n * kAdjLanes, 128) * 4, nw_i = nblk(n, 256) * 8;
+  double *tpart_f, *tpart_i, *tsnap;
   float* coef;
   uint32_t *start0, *start_end;  // cell starts of the first and last state of the window
-  ACU(buf.alloc(&start0, (size_t)E.ncells + 1));
-  ACU(buf.alloc(&start_end, (size_t)E.ncells + 1));
+  float4* stage = nullptr;       // id-ordered copy of three per-particle arrays (record API)
   const size_t start_bytes = sizeof(uint32_t) * ((size_t)E.ncells + 1);
-  ACU(buf.alloc(&acc, 2 * (size_t)nbins));
-  ACU(buf.alloc(&theta, 3));
-  ACU(buf.alloc(&coef, nbins));
+  auto layout = [&](Carve& c) {
+    for (auto& A : tape) {
+      c.alloc(&A.pos, n);
+      c.alloc(&A.vt, n);
+      c.alloc(&A.vel, n);
+      c.alloc(&A.frc, n);
+    }
+    for (int k = 0; k < T; ++k) {
+      c.alloc(&tperm[k], n);
+      c.alloc(&tstart[k], (size_t)E.ncells + 1);
+    }
+    for (int q2 = 0; q2 <= nseg; ++q2) {
+      if (whole) {
+        ck[q2] = tape[q2 * K];
+        continue;
+      }
+      Arrays& A = ck[q2];
+      c.alloc(&A.pos, n);
+      c.alloc(&A.vt, n);
+      c.alloc(&A.vel, n);
+      c.alloc(&A.frc, n);
+    }
+    for (int q = 0; q < 2; ++q) {
+      c.alloc(&rb[q], n);
+      c.alloc(&vb[q], n);
+      c.alloc(&fb[q], n);
+    }
+    c.alloc(&Rb, n);
+    c.alloc(&Vb, n);
+    c.alloc(&zero4, n);
+    c.alloc(&start0, (size_t)E.ncells + 1);
+    c.alloc(&start_end, (size_t)E.ncells + 1);
+    c.alloc(&acc, 2 * (size_t)nbins);
+    c.alloc(&tpart_f, 2 * (size_t)nw_f);
+    c.alloc(&tpart_i, (size_t)nw_i);
+    c.alloc(&tsnap, 3 * (size_t)(nseg + 1));
+    c.alloc(&coef, nbins);
+    if (rec) c.alloc(&stage, 3 * (size_t)n);
+  };
+  {
+    Carve sizing;
+    layout(sizing);
+    if (sizing.off > h->adj_ws_bytes) {
+      cudaFree(h->d_adj_ws);
+      h->d_adj_ws = nullptr;
+      h->adj_ws_bytes = 0;
+      ACU(cudaMalloc(&h->d_adj_ws, sizing.off));
+      h->adj_ws_bytes = sizing.off;
+    }
+    Carve c;
+    c.base = static_cast<char*>(h->d_adj_ws);
+    layout(c);
+  }
   DevCounters ctr0, ctr_end;
 
   auto copy_state = [&](const Arrays& dst, const Arrays& src) -> cudaError_t {
@@ -540,7 +596,7 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
                                                  make_float3(P.vw[0], P.vw[1], P.vw[2]));
     engine_enqueue_force(E, 0);
   }
-  ACU(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * nbins, st));
+  ACU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * nbins, st));
   ACU(copy_state(ck[0], E.arr[E.cur]));
   ACU(cudaMemcpyAsync(start0, E.cl.start, start_bytes, cudaMemcpyDeviceToDevice, st));
   for (int s = 1; s <= nsteps; ++s) {
@@ -557,8 +613,8 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   }
   ACU(cudaGetLastError());
   ACU(cudaMemcpyAsync(start_end, E.cl.start, start_bytes, cudaMemcpyDeviceToDevice, st));
-  std::vector<double> hacc(2 * nbins);
-  ACU(cudaMemcpyAsync(hacc.data(), acc, sizeof(double) * 2 * nbins, cudaMemcpyDeviceToHost, st));
+  std::vector<unsigned long long> hacc(2 * nbins);
+  ACU(cudaMemcpyAsync(hacc.data(), acc, sizeof(unsigned long long) * 2 * nbins, cudaMemcpyDeviceToHost, st));
   ACU(cudaMemcpyAsync(&ctr_end, E.d_ctr, sizeof ctr_end, cudaMemcpyDeviceToHost, st));
   ACU(cudaStreamSynchronize(st));
   if (ctr_end.status) return engine_status_code(E, ctr_end.status);
@@ -566,17 +622,15 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   double L = 0.0;
   std::vector<float> hcoef(nbins, 0.0f);
   for (int b = 0; b < nbins; ++b) {
-    const double cnt = hacc[2 * b];
+    const double cnt = (double)hacc[2 * b];
     if (cnt <= 0) continue;
-    const double u = hacc[2 * b + 1] / cnt;
+    const double u = (double)(long long)hacc[2 * b + 1] / kBinFix / cnt;
     L += (u - target[b]) * (u - target[b]);
     hcoef[b] = (float)(2.0 * (u - target[b]) / cnt);
   }
   ACU(cudaMemcpyAsync(coef, hcoef.data(), sizeof(float) * nbins, cudaMemcpyHostToDevice, st));
-  float4* stage = nullptr;  // id-ordered copy of three per-particle arrays
   const size_t rec_floats = (size_t)12 * n;
   if (rec) {
-    ACU(buf.alloc(&stage, 3 * (size_t)n));
     if (rec->coef) memcpy(rec->coef, hcoef.data(), sizeof(float) * nbins);
     if (rec->seg_step)
       for (int q2 = 0; q2 <= nseg; ++q2) rec->seg_step[q2] = step0 + (uint32_t)(q2 * K);
@@ -587,9 +641,8 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
                             cudaMemcpyDeviceToHost, st));
       }
   }
-  // per-segment parameter gradient: theta after each segment's reversal
-  std::vector<double> theta_snap(3 * (size_t)(nseg + 1), 0.0);
-  ACU(cudaMemsetAsync(theta, 0, 3 * sizeof(double), st));
+  ACU(cudaMemsetAsync(tpart_f, 0, sizeof(double) * 2 * (size_t)nw_f, st));
+  ACU(cudaMemsetAsync(tpart_i, 0, sizeof(double) * (size_t)nw_i, st));
   ACU(cudaMemsetAsync(zero4, 0, nf4, st));
 
   // ---- backward --------------------------------------------------------------
@@ -626,18 +679,16 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
       const Arrays& An = tape[base + k + 1];
       const Arrays& Ao = tape[base + k];
       k_adj_force<<<nblk((long)n * kAdjLanes, 128), 128, 0, st>>>(P, An.pos, An.vt, tstart[base + k], n, step_new, rb[q],
-                                                vb[q], fb[q], Rb, Vb, tie, theta, E.d_ctr);
+                                                vb[q], fb[q], Rb, Vb, tie, tpart_f, E.d_ctr);
       const int s_old = seg * K + k;  // global index of the previous state
       k_adj_integrate<<<nblk(n, 256), 256, 0, st>>>(P, Ao.pos, Ao.vel, Ao.frc, An.pos, An.vt,
                                                     tperm[base + k], n, Rb, Vb, vb[q], rb[q ^ 1],
                                                     vb[q ^ 1], fb[q ^ 1], B, s_old >= 1 ? coef : nullptr,
-                                                    theta);
+                                                    tpart_i);
       q ^= 1;
     }
-    if (rec && rec->seg_grad && seg > 0) {
-      ACU(cudaMemcpyAsync(&theta_snap[3 * (size_t)seg], theta, 3 * sizeof(double),
-                          cudaMemcpyDeviceToHost, st));
-    }
+    if (rec && rec->seg_grad && seg > 0)
+      k_theta_sum<<<1, kThetaThreads, 0, st>>>(tpart_f, nw_f, tpart_i, nw_i, tsnap + 3 * seg);
   }
   if (rec && rec->adj) {
     k_unsort3<<<nblk(n, 256), 256, 0, st>>>(ck[0].pos, rb[q], vb[q], fb[q], n, stage);
@@ -647,11 +698,14 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   {
     const Arrays& A0 = ck[0];
     k_adj_force<<<nblk((long)n * kAdjLanes, 128), 128, 0, st>>>(P, A0.pos, A0.vt, start0, n, step0, zero4, zero4,
-                                              fb[q], Rb, Vb, tie, theta, E.d_ctr);
+                                              fb[q], Rb, Vb, tie, tpart_f, E.d_ctr);
   }
+  k_theta_sum<<<1, kThetaThreads, 0, st>>>(tpart_f, nw_f, tpart_i, nw_i, tsnap);
   ACU(cudaGetLastError());
-  double th[3];
-  ACU(cudaMemcpyAsync(th, theta, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> theta_snap(3 * (size_t)(nseg + 1), 0.0);
+  const size_t nsnap = (rec && rec->seg_grad) ? 3 * (size_t)nseg : 3;
+  ACU(cudaMemcpyAsync(theta_snap.data(), tsnap, sizeof(double) * nsnap, cudaMemcpyDeviceToHost, st));
+  const double* th = theta_snap.data();
   // a recomputed segment whose scan timed out leaves its status (nothing else sets one:
   // the forward window ran the same steps without error)
   DevCounters ctr_bwd;
@@ -673,8 +727,6 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
     // segment k's share: theta accumulated while reversing it (segment 0 also holds
     // the dependence of f(0) on the parameters); snapshots were taken after the
     // reversal of segments nseg-1 .. 1
-    for (int k2 = 0; k2 < 3; ++k2) theta_snap[3 * (size_t)nseg + k2] = 0.0;
-    for (int k2 = 0; k2 < 3; ++k2) theta_snap[k2] = th[k2];
     for (int seg = 0; seg < nseg; ++seg) {
       const double* after = &theta_snap[3 * (size_t)seg];
       const double* before = &theta_snap[3 * (size_t)(seg + 1)];

@@ -547,6 +547,9 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
   } else if (k == "adjoint_tape_mb") {
     if (!(v >= 0.0)) return fail(h, DPD_EINVAL, "adjoint_tape_mb must be >= 0");
     h->adjoint_tape_mb = v;
+    cudaFree(h->d_adj_ws);  // the next window sizes its workspace anew
+    h->d_adj_ws = nullptr;
+    h->adj_ws_bytes = 0;
   } else if (k == "scan_stall_tile") {
     if (v < -1 || v != std::floor(v) || v > 1e9)
       return fail(h, DPD_EINVAL, "scan_stall_tile must be -1 or a tile index");
@@ -618,6 +621,7 @@ int dpd_set_stream(dpd_t* h, void* stream) {
 int dpd_destroy(dpd_t* h) {
   if (!h) return DPD_OK;
   dpd::engine_free(h->E);
+  cudaFree(h->d_adj_ws);
   cudaFree(h->d_out4);
   cudaFree(h->d_out_id);
   cudaFree(h->d_out_type);

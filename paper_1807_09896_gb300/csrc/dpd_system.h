@@ -32,6 +32,10 @@ struct dpd_system {
   uint32_t sys = 0;
   int reflect_variant = 0;
   double adjoint_tape_mb = 2048.0;  // budget for keeping a whole adjoint window's record
+  // the adjoint's device workspace (record, checkpoints, adjoint arrays): kept between
+  // windows, grown when a window needs more, freed by dpd_destroy or adjoint_tape_mb
+  void* d_adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
   int sample_every = 0;
   int nc[3] = {0, 0, 0};
   int ncells = 0;
