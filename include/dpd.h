@@ -65,7 +65,8 @@ enum {
   DPD_ESTATE = -4,   /* call out of order (e.g. dpd_step before dpd_set_particles) */
   DPD_ELOST = -5,    /* a fluid particle was found at phi < 0 */
   DPD_EBAND = -6,    /* a drift exceeded the band margin of the reflection test */
-  DPD_ETIMEOUT = -7, /* a bounded device wait gave up (the cell scan's look-back) */
+  DPD_ETIMEOUT = -7, /* reserved for a bounded device wait that gives up: no kernel of
+                        this library waits on another block, so none is returned */
   DPD_ENAN = -8,     /* a non-finite position, velocity or force appeared */
   DPD_EOVERFLOW = -9 /* a size limit was exceeded (e.g. a cell holds too many particles) */
 };
@@ -251,11 +252,7 @@ int dpd_get_stats(dpd_t* h, double out[8]);
  * parameters), "step" (the step counter, part of the noise counter), "use_graph" (1: replay
  * steps from a CUDA graph), "graph_steps" (even number of steps per graph,
  * default 20), "force_variant" (launch shape of the pair-force kernel, see
- * dpd_autotune), "adjoint_tape_mb" (see dpd_adjoint_window), "scan_stall_tile" (a
- * test hook, default -1: tile k >= 0 of the single-pass cell scan publishes
- * nothing, so the tiles after it give up waiting and the step returns
- * DPD_ETIMEOUT; the force kernels skip that step and the state stays invalid
- * until the next dpd_set_particles).
+ * dpd_autotune), "adjoint_tape_mb" (see dpd_adjoint_window).
  * Read-only (dpd_get_option): "ncells", "kernel_launches" (kernels
  * enqueued by stepping calls so far), "kernels_per_step", "force_variants",
  * "force_newton3" (1 if the current shape evaluates each pair once), "scan_tiles"

@@ -152,14 +152,14 @@ __global__ void __launch_bounds__(128)
 k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restrict__ vt,
             const uint32_t* __restrict__ start, int n, uint32_t step, const float4* __restrict__ rbar,
             const float4* __restrict__ vbar, const float4* __restrict__ fbar, float4* Rb, float4* Vb,
-            float tie_coef, double* tpart, const DevCounters* ctr) {
+            float tie_coef, double* tpart) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / kAdjLanes, sub = t % kAdjLanes;
   double ta = 0.0, tg = 0.0;
   float Rx = 0.f, Ry = 0.f, Rz = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
   bool target = false;
   // cell starts left by a timed-out scan are not a valid prefix (the status reports it)
-  if (i < n && !scan_failed(ctr)) {
+  if (i < n) {
     const float4 pi = pos[i];
     target = !is_solid(pi.w);
     if (target && sub < 3) {
@@ -241,7 +241,7 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
     Uy += __shfl_xor_sync(0xffffffffu, Uy, o);
     Uz += __shfl_xor_sync(0xffffffffu, Uz, o);
   }
-  if (i < n && sub == 0 && !scan_failed(ctr)) {
+  if (i < n && sub == 0) {
     Rb[i] = target ? make_float4(Rx, Ry, Rz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     Vb[i] = target ? make_float4(Ux, Uy, Uz, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -679,7 +679,7 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
       const Arrays& An = tape[base + k + 1];
       const Arrays& Ao = tape[base + k];
       k_adj_force<<<nblk((long)n * kAdjLanes, 128), 128, 0, st>>>(P, An.pos, An.vt, tstart[base + k], n, step_new, rb[q],
-                                                vb[q], fb[q], Rb, Vb, tie, tpart_f, E.d_ctr);
+                                                vb[q], fb[q], Rb, Vb, tie, tpart_f);
       const int s_old = seg * K + k;  // global index of the previous state
       k_adj_integrate<<<nblk(n, 256), 256, 0, st>>>(P, Ao.pos, Ao.vel, Ao.frc, An.pos, An.vt,
                                                     tperm[base + k], n, Rb, Vb, vb[q], rb[q ^ 1],
@@ -698,7 +698,7 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   {
     const Arrays& A0 = ck[0];
     k_adj_force<<<nblk((long)n * kAdjLanes, 128), 128, 0, st>>>(P, A0.pos, A0.vt, start0, n, step0, zero4, zero4,
-                                              fb[q], Rb, Vb, tie, tpart_f, E.d_ctr);
+                                              fb[q], Rb, Vb, tie, tpart_f);
   }
   k_theta_sum<<<1, kThetaThreads, 0, st>>>(tpart_f, nw_f, tpart_i, nw_i, tsnap);
   ACU(cudaGetLastError());
@@ -706,12 +706,12 @@ static int adjoint_window(dpd_t* h, int nsteps, int ckpt_every, int axis, double
   const size_t nsnap = (rec && rec->seg_grad) ? 3 * (size_t)nseg : 3;
   ACU(cudaMemcpyAsync(theta_snap.data(), tsnap, sizeof(double) * nsnap, cudaMemcpyDeviceToHost, st));
   const double* th = theta_snap.data();
-  // a recomputed segment whose scan timed out leaves its status (nothing else sets one:
-  // the forward window ran the same steps without error)
+  // recomputed segments repeat steps the forward window ran without error; a status
+  // set now would mean the record and the state disagree
   DevCounters ctr_bwd;
   ACU(cudaMemcpyAsync(&ctr_bwd, E.d_ctr, sizeof ctr_bwd, cudaMemcpyDeviceToHost, st));
   ACU(cudaStreamSynchronize(st));
-  if (ctr_bwd.status & ST_TIMEOUT) return engine_status_code(E, ctr_bwd.status);
+  if (ctr_bwd.status) return engine_status_code(E, ctr_bwd.status);
   // ---- leave the system at the end of the window, as dpd_step would ----------
   ACU(copy_state(E.arr[E.cur], ck[nseg]));
   ACU(cudaMemcpyAsync(E.cl.start, start_end, start_bytes, cudaMemcpyDeviceToDevice, st));

@@ -550,10 +550,6 @@ int dpd_set_option(dpd_t* h, const char* key, double v) {
     cudaFree(h->d_adj_ws);  // the next window sizes its workspace anew
     h->d_adj_ws = nullptr;
     h->adj_ws_bytes = 0;
-  } else if (k == "scan_stall_tile") {
-    if (v < -1 || v != std::floor(v) || v > 1e9)
-      return fail(h, DPD_EINVAL, "scan_stall_tile must be -1 or a tile index");
-    E.scan_stall_tile = (int)v;
   } else {
     return fail(h, DPD_EINVAL, "unknown option '%s'", key);
   }
@@ -596,7 +592,6 @@ int dpd_get_option(dpd_t* h, const char* key, double* v) {
   else if (k == "force_variant") *v = E.force_variant;
   else if (k == "force_variants") *v = dpd::force_variants();
   else if (k == "force_newton3") *v = dpd::force_variant_newton3(E.force_variant);
-  else if (k == "scan_stall_tile") *v = E.scan_stall_tile;
   else if (k == "adjoint_tape_mb") *v = h->adjoint_tape_mb;
   else if (k == "scan_tiles") *v = dpd::scan_blocks(h->ncells);
   else return fail(h, DPD_EINVAL, "unknown option '%s'", key);

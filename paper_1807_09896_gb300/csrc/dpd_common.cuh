@@ -27,7 +27,6 @@ enum : uint32_t {
   ST_LOST = 4u,      // fluid particle at phi < 0
   ST_OVERFLOW = 8u,  // a cell exceeded the per-cell sort capacity
   ST_BADID = 16u,    // ids are not a permutation of 0..n-1
-  ST_TIMEOUT = 32u,  // a bounded device wait gave up (the cell scan's look-back)
 };
 
 struct DevCounters {
@@ -36,12 +35,6 @@ struct DevCounters {
   unsigned long long reflections;
   unsigned long long fallbacks;
 };
-
-// True when a timed-out cell scan left the cell starts unusable: kernels that index
-// through them do nothing (the status makes the step report DPD_ETIMEOUT).
-__device__ __forceinline__ bool scan_failed(const DevCounters* ctr) {
-  return (ctr->status & ST_TIMEOUT) != 0u;
-}
 
 // Fixed-point pair sums of the Newton's-third-law force shapes: 2^32 units per
 // force unit, one array of n per component, holding the shares -f_ij handed to
@@ -142,12 +135,23 @@ struct CellList {
   uint32_t* count;  // particles per cell (zeroed by the scan)
   uint32_t* start;  // exclusive prefix of count, ncells + 1 entries
   uint32_t* perm;   // new position -> old position
-  // single-pass scan: one published word per tile of cells, and the ticket counter
-  // that numbers the tiles in the order their blocks start (never reset between
-  // launches: ticket / tiles is the launch's epoch)
-  unsigned long long* tile;
-  unsigned long long* ticket;
+  // the scan's tiles of kScanTileCells cells: the particles each tile's cells hold,
+  // added by the kernels that fill count, read by the scan, cleared by the scatter
+  uint32_t* tile_total;
 };
+
+// Cells per tile of the cell scan (one block of the scan per tile).  Each tile's total
+// is kept in kTileShards counters (by warp), each on its own 128-byte line, so that the
+// producers' atomics spread over the L2 instead of queueing on a few lines.
+constexpr int kScanTileCells = 2048;
+constexpr int kTileShards = 4;
+constexpr int kTileStride = 32;  // uint32 words between counters (128 bytes)
+__host__ __device__ constexpr size_t tile_total_words(int ntiles) {
+  return (size_t)ntiles * kTileShards * kTileStride;
+}
+__device__ __forceinline__ uint32_t* tile_counter(uint32_t* tt, uint32_t tile, int warp) {
+  return tt + ((size_t)tile * kTileShards + (uint32_t)(warp & (kTileShards - 1))) * kTileStride;
+}
 
 __device__ __forceinline__ uint32_t tag_of(float w) { return __float_as_uint(w); }
 __device__ __forceinline__ bool is_solid(float w) { return (tag_of(w) & kSolidBit) != 0u; }

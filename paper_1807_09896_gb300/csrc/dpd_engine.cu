@@ -61,10 +61,9 @@ static void free_particle_buffers(Engine& E) {
 static void free_cell_buffers(Engine& E) {
   cudaFree(E.cl.count);
   cudaFree(E.cl.start);
-  cudaFree(E.cl.tile);
-  cudaFree(E.cl.ticket);
+  cudaFree(E.cl.tile_total);
   E.cl.count = E.cl.start = nullptr;
-  E.cl.tile = E.cl.ticket = nullptr;
+  E.cl.tile_total = nullptr;
   E.cell_cap = 0;
 }
 
@@ -104,16 +103,8 @@ int engine_reserve(Engine& E, int nsys, int n, int ncells) {
     free_cell_buffers(E);
     ECU(E, dev_alloc(&E.cl.count, ncells));
     ECU(E, dev_alloc(&E.cl.start, (size_t)ncells + 1));
-    ECU(E, dev_alloc(&E.cl.tile, scan_blocks(ncells)));
-    ECU(E, dev_alloc(&E.cl.ticket, 1));
-    ECU(E, cudaMemsetAsync(E.cl.tile, 0, sizeof(unsigned long long) * scan_blocks(ncells), E.stream));
+    ECU(E, dev_alloc(&E.cl.tile_total, tile_total_words(scan_blocks(ncells))));
     E.cell_cap = ncells;
-  }
-  if (ncells != E.ncells) {
-    // the ticket numbers launches of one tile count: restart it, and clear the published
-    // words, whose epochs would otherwise repeat
-    ECU(E, cudaMemsetAsync(E.cl.ticket, 0, sizeof(unsigned long long), E.stream));
-    ECU(E, cudaMemsetAsync(E.cl.tile, 0, sizeof(unsigned long long) * scan_blocks(ncells), E.stream));
   }
   if (n > E.cap) {
     engine_free_graphs(E);
@@ -134,8 +125,10 @@ int engine_reserve(Engine& E, int nsys, int n, int ncells) {
   E.nsys = nsys;
   E.n = n;
   E.ncells = ncells;
-  // counts must start at zero; every scan leaves them at zero
+  // counts and tile totals must start at zero; every scan leaves them at zero
   ECU(E, cudaMemsetAsync(E.cl.count, 0, sizeof(uint32_t) * (ncells > 0 ? ncells : 1), E.stream));
+  ECU(E, cudaMemsetAsync(E.cl.tile_total, 0, sizeof(uint32_t) * tile_total_words(scan_blocks(ncells)),
+                         E.stream));
   return DPD_OK;
 }
 
@@ -148,7 +141,7 @@ int engine_upload_sys(Engine& E) {
 
 void engine_enqueue_sort(Engine& E) {
   launch_key(E.d_sys, E.nsys, E.arr[E.cur], E.cl, E.n, E.stream);
-  launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
+  launch_scan(E.cl, E.ncells, E.n, E.stream);
   launch_sort(E.cl, E.arr[E.cur], E.arr[E.cur ^ 1], E.n, E.ncells, E.d_ctr, E.stream);
   E.cur ^= 1;
 }
@@ -178,7 +171,7 @@ static void enqueue_step_from(Engine& E, int c, bool finish) {
   const Arrays& B = E.arr[c ^ 1];
   launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.sums_pending, E.n, E.d_ctr,
                    E.stream);
-  launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
+  launch_scan(E.cl, E.ncells, E.n, E.stream);
   launch_sort(E.cl, A, B, E.n, E.ncells, E.d_ctr, E.stream);
   launch_force_pairs(E.h_sys[0].P, E.d_sys, E.nsys, B, E.cl.start, E.facc, E.n, E.d_ctr, 1,
                      E.force_variant, E.stream);
@@ -276,9 +269,9 @@ int engine_time_phases(Engine& E, int nsteps, double* ms) {
     launch_integrate(E.h_sys[0].P, E.d_sys, E.nsys, A, E.cl, E.facc, E.sums_pending, E.n, E.d_ctr,
                      E.stream);
     cudaEventRecord(ev[1], E.stream);
-    launch_scan(E.cl, E.ncells, E.n, E.d_ctr, E.nsys, E.scan_stall_tile, E.stream);
+    launch_scan(E.cl, E.ncells, E.n, E.stream);
     cudaEventRecord(ev[2], E.stream);
-    launch_scatter(E.cl, E.n, E.d_ctr, E.stream);
+    launch_scatter(E.cl, E.n, E.ncells, E.d_ctr, E.stream);
     cudaEventRecord(ev[3], E.stream);
     launch_cell_sort(E.cl, E.n, E.ncells, E.d_ctr, E.stream);
     cudaEventRecord(ev[4], E.stream);
@@ -386,12 +379,6 @@ int engine_read_counters(Engine& E, uint32_t* status) {
 
 int engine_status_code(Engine& E, uint32_t st) {
   if (st == 0) return DPD_OK;
-  // a timed-out scan leaves invalid cell starts, whose consequences (an overflow, a lost
-  // or non-finite particle) it would otherwise hide behind: it goes first
-  if (st & ST_TIMEOUT)
-    return engine_fail(E, DPD_ETIMEOUT,
-                       "the cell scan's look-back gave up waiting for a tile (nothing was updated "
-                       "past it; reload the state)");
   if (st & ST_NAN) return engine_fail(E, DPD_ENAN, "non-finite position, velocity or force");
   if (st & ST_LOST) return engine_fail(E, DPD_ELOST, "a fluid particle is at phi < 0");
   if (st & ST_BADID) return engine_fail(E, DPD_EINVAL, "ids are not a permutation of 0..n-1");

@@ -41,7 +41,6 @@ struct Engine {
   StepParams graph_P = {};
   int graph_n = -1, graph_ncells = -1, graph_nsys = -1, graph_variant = -1, graph_len = -1;
   int use_graph = 1, graph_steps = 20, force_variant = 0;
-  int scan_stall_tile = -1;  // test hook of the cell scan (see launch_scan)
   // the last step enqueued ran a Newton's-third-law force kernel and left its force in
   // the fixed-point sums for the next drift (which then runs in its pending form)
   bool sums_pending = false;

@@ -368,12 +368,10 @@ k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   const float4 pi = A.pos[i];
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
-    if (scan_failed(ctrs + sk)) return;
     force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, A,
                                                           facc, (size_t)n, i, pi, ctrs + sk, list,
                                                           seg_b, seg_e);
   } else {
-    if (scan_failed(ctrs)) return;
     force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, A, facc, (size_t)n, i, pi,
                                                           ctrs, list, seg_b, seg_e);
   }
@@ -426,11 +424,9 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   }
   if constexpr (kBatch) {
     const int sk = sys_of(S, nsys, (uint32_t)i);
-    if (scan_failed(ctrs + sk)) return;
     force_body<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,
                                                        A, i, pi, list, seg_b, seg_e, kick);
   } else {
-    if (scan_failed(ctrs)) return;
     force_body<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, ctrs, A, i, pi, list, seg_b,
                                                        seg_e, kick);
   }

@@ -159,6 +159,17 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
   if (lane == leader) base = atomicAdd(&C.count[c], (uint32_t)__popc(peers));
   base = __shfl_sync(active, base, leader);
   C.rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  // the scan's tile totals, one atomic per tile the warp touches (usually one)
+  const uint32_t tl = c / (uint32_t)kScanTileCells;
+  const int first = __ffs(active) - 1;
+  const uint32_t tl0 = __shfl_sync(active, tl, first);
+  if (__all_sync(active, tl == tl0)) {
+    if (lane == first) atomicAdd(tile_counter(C.tile_total, tl0, i >> 5), (uint32_t)__popc(active));
+  } else {
+    const unsigned tpeers = __match_any_sync(active, tl);
+    if (lane == __ffs(tpeers) - 1)
+      atomicAdd(tile_counter(C.tile_total, tl, i >> 5), (uint32_t)__popc(tpeers));
+  }
 }
 
 // A single system takes its parameters by value (kernel-parameter bank); a batch
@@ -197,27 +208,25 @@ __global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellLis
   const uint32_t c = S[sk].cell_off + (uint32_t)cell_of(S[sk].P, p.x, p.y, p.z);
   C.key[i] = (uint32_t)c;
   C.rank[i] = atomicAdd(&C.count[c], 1u);
+  atomicAdd(tile_counter(C.tile_total, c / (uint32_t)kScanTileCells, i >> 5), 1u);
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of the per-cell counts in one pass (decoupled look-back, Merrill
-// and Garland 2016).  Blocks take tiles of kScanChunk cells in the order they start
-// (a ticket), so every tile's predecessors are running or done.  A tile publishes
-// its own total, looks back over its predecessors' published words (a warp reads 32
-// at a time) until it meets an inclusive prefix, publishes its own inclusive prefix
-// and writes its starts.  A published word is (epoch, flag, value) in 64 bits; the
-// epoch is the launch's ticket count / tiles, so words of an earlier launch read as
-// "not yet published" and nothing needs clearing between launches.  Every wait is
-// bounded: after kScanSpinLimit polls the tile sets ST_TIMEOUT in every system's
-// status and carries on with what it has; the kernels that index through the starts
-// check that bit first and do nothing, so a timed-out scan cannot drive them out of
-// range.  The scan also zeroes the counts for the next step.
+// Exclusive scan of the per-cell counts in one launch, with no block waiting on
+// another.  One block per tile of kScanTileCells cells.  The kernels that fill the
+// counts also add each particle to its tile's total (one warp-aggregated atomic per
+// tile a warp touches), so a block finds the prefix before its tile by summing the
+// totals of the tiles before it: independent loads, all in flight at once.  A
+// decoupled look-back (Merrill and Garland 2016) has to learn the same sum from its
+// predecessors' published words while they run; on GB300 its chain of release
+// stores and acquire polls took 11-13 us for the 340k cells of the 1M-particle
+// channel whatever the tile shape.  The scan zeroes the counts for the next step and
+// the scatter, which follows every scan, zeroes the tile totals.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 8;
 constexpr int kScanChunk = kScanThreads * kScanPerThread;
-constexpr int kScanSpinLimit = 4096;
-constexpr uint32_t kTileAggregate = 1u, kTilePrefix = 2u;
+static_assert(kScanChunk == kScanTileCells, "one scan block per tile");
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const int lane = threadIdx.x & 31;
@@ -229,114 +238,86 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   return v;
 }
 
-// Block-wide exclusive scan of one value per thread; returns the block total in *total.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t warp_tot[kScanThreads / 32];
+// Block-wide exclusive scan of one value per thread, plus the block sum of a second
+// value; returns the scan, the block total in *total and the second sum in *sum2.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t v2, uint32_t* total,
+                                                    uint32_t* sum2) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32], warp_tot2[kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t inc = warp_incl_scan(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
   if (lane == 31) warp_tot[warp] = inc;
+  if (lane == 0) warp_tot2[warp] = v2;
   __syncthreads();
   if (warp == 0) {
     uint32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+    uint32_t t2 = lane < kScanThreads / 32 ? warp_tot2[lane] : 0u;
     t = warp_incl_scan(t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
     if (lane < kScanThreads / 32) warp_tot[lane] = t;
+    if (lane == 0) warp_tot2[0] = t2;
   }
   __syncthreads();
   const uint32_t base = warp > 0 ? warp_tot[warp - 1] : 0u;
   *total = warp_tot[kScanThreads / 32 - 1];
-  __syncthreads();
+  *sum2 = warp_tot2[0];
   return base + inc - v;
 }
 
-__device__ __forceinline__ unsigned long long tile_word(uint32_t epoch, uint32_t flag, uint32_t v) {
-  return ((unsigned long long)((epoch << 2) | flag) << 32) | v;
-}
-
-__device__ __forceinline__ void publish(unsigned long long* w, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(w), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long peek(const unsigned long long* w) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
-  return v;
-}
-
-// stall_tile >= 0 (a test hook, set only through an option): that tile publishes
-// nothing, so its successors' look-back runs out and the launch reports ST_TIMEOUT.
 __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t* count, int m, uint32_t* start,
-                                                       uint32_t n_total, unsigned long long* tiles,
-                                                       unsigned long long* ticket, int ntiles,
-                                                       DevCounters* ctrs, int nsys, int stall_tile) {
-  __shared__ unsigned long long s_ticket;
-  __shared__ uint32_t s_excl;
-  if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1ull);
-  __syncthreads();
-  const int t = (int)(s_ticket % (unsigned long long)ntiles);
-  const uint32_t epoch = (uint32_t)((s_ticket / (unsigned long long)ntiles + 1ull) & 0x3fffffffull);
+                                                       uint32_t n_total,
+                                                       const uint32_t* __restrict__ tile_total,
+                                                       int ntiles) {
+  const int t = blockIdx.x;
   const int base = t * kScanChunk + threadIdx.x * kScanPerThread;
+  static_assert(kScanPerThread % 4 == 0, "counts move as uint4");
   uint32_t v[kScanPerThread];
+  const bool full = base + kScanPerThread <= m;  // base is a multiple of 4: 16-byte aligned
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; k += 4) {
+      const uint4 q = *reinterpret_cast<const uint4*>(count + base + k);
+      v[k] = q.x;
+      v[k + 1] = q.y;
+      v[k + 2] = q.z;
+      v[k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanPerThread; ++k) v[k] = (base + k < m) ? count[base + k] : 0u;
+  }
+  // the particles of the tiles before this one
+  uint32_t pre = 0;
+  for (int j = threadIdx.x; j < t * kTileShards; j += kScanThreads) pre += tile_total[(size_t)j * kTileStride];
   uint32_t sum = 0;
 #pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k) {
-    v[k] = (base + k < m) ? count[base + k] : 0u;
-    sum += v[k];
-  }
-  uint32_t total;
-  const uint32_t local = block_excl_scan(sum, &total);
-  const bool stalled = t == stall_tile;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    if (lane == 0 && !stalled)
-      publish(&tiles[t], tile_word(epoch, t == 0 ? kTilePrefix : kTileAggregate, total));
-    uint32_t excl = 0;
-    bool timed_out = false;
-    int end = t - 1;  // the window is tiles end - 31 .. end, lane 0 the nearest
-    int polls = 0;
-    while (end >= 0) {
-      const int j = end - lane;
-      uint32_t flag = kTilePrefix, val = 0;  // before tile 0: an inclusive prefix of 0
-      if (j >= 0) {
-        const unsigned long long w = peek(&tiles[j]);
-        const uint32_t hi = (uint32_t)(w >> 32);
-        flag = (hi >> 2) == epoch ? (hi & 3u) : 0u;
-        val = (uint32_t)w;
-      }
-      const unsigned pmask = __ballot_sync(0xffffffffu, flag == kTilePrefix);
-      const unsigned xmask = __ballot_sync(0xffffffffu, flag == 0u);
-      const int first_p = pmask ? __ffs(pmask) - 1 : 32;
-      const unsigned before = first_p == 32 ? 0xffffffffu : ((1u << first_p) - 1u);
-      if (xmask & before) {  // a nearer predecessor has not published yet: wait
-        if (++polls > kScanSpinLimit) {
-          timed_out = true;
-          break;
-        }
-        __nanosleep(64);
-        continue;
-      }
-      uint32_t part = lane <= first_p ? val : 0u;
+  for (int k = 0; k < kScanPerThread; ++k) sum += v[k];
+  uint32_t total, excl;
+  const uint32_t local = block_excl_scan(sum, pre, &total, &excl);
+  uint32_t run = excl + local;
+  if (full) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      excl += part;
-      if (first_p < 32) break;
-      end -= 32;
+    for (int k = 0; k < kScanPerThread; k += 4) {
+      uint4 q;
+      q.x = run;
+      q.y = q.x + v[k];
+      q.z = q.y + v[k + 1];
+      q.w = q.z + v[k + 2];
+      run = q.w + v[k + 3];
+      *reinterpret_cast<uint4*>(start + base + k) = q;
+      *reinterpret_cast<uint4*>(count + base + k) = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (lane == 0) {
-      if (t > 0 && !stalled) publish(&tiles[t], tile_word(epoch, kTilePrefix, excl + total));
-      if (timed_out)
-        for (int k = 0; k < nsys; ++k) atomicOr(&ctrs[k].status, ST_TIMEOUT);
-      s_excl = excl;
-    }
-  }
-  __syncthreads();
-  uint32_t run = s_excl + local;
+  } else {
 #pragma unroll
-  for (int k = 0; k < kScanPerThread; ++k) {
-    if (base + k < m) {
-      start[base + k] = run;
-      count[base + k] = 0u;
+    for (int k = 0; k < kScanPerThread; ++k) {
+      if (base + k < m) {
+        start[base + k] = run;
+        count[base + k] = 0u;
+      }
+      run += v[k];
     }
-    run += v[k];
   }
   if (t == ntiles - 1 && threadIdx.x == 0) start[m] = n_total;
 }
@@ -345,8 +326,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t* count, int m, u
 // Counting-sort scatter, per-cell order, and the gather that reorders the
 // particle arrays into cell order.
 // ---------------------------------------------------------------------------
-__global__ void k_scatter(CellList C, int n, DevCounters* ctr) {
+// It also clears the scan's tile totals (ntw counters) for the next step's producers:
+// the scan, the only reader, has finished.
+__global__ void k_scatter(CellList C, int n, int ntw, DevCounters* ctr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int q = i; q < ntw; q += gridDim.x * blockDim.x) C.tile_total[(size_t)q * kTileStride] = 0u;
   if (i >= n) return;
   const uint32_t d = C.start[C.key[i]] + C.rank[i];
   if (d < (uint32_t)n)
@@ -639,15 +623,14 @@ int scan_blocks(int ncells) { return ncells > 0 ? blocks(ncells, kScanChunk) : 1
 
 int scan_kernels(int) { return 1; }
 
-void launch_scan(const CellList& C, int ncells, int n, DevCounters* ctr, int nsys, int stall_tile,
-                 cudaStream_t s) {
+void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s) {
   const int nt = scan_blocks(ncells);
-  k_scan<<<nt, kScanThreads, 0, s>>>(C.count, ncells, C.start, (uint32_t)n, C.tile, C.ticket, nt, ctr,
-                                     nsys, stall_tile);
+  k_scan<<<nt, kScanThreads, 0, s>>>(C.count, ncells, C.start, (uint32_t)n, C.tile_total, nt);
 }
 
-void launch_scatter(const CellList& C, int n, DevCounters* ctr, cudaStream_t s) {
-  if (n > 0) k_scatter<<<blocks(n, 256), 256, 0, s>>>(C, n, ctr);
+// With no particles nothing fills the counts, so the tile totals stay zero.
+void launch_scatter(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s) {
+  if (n > 0) k_scatter<<<blocks(n, 256), 256, 0, s>>>(C, n, scan_blocks(ncells) * kTileShards, ctr);
 }
 
 void launch_cell_sort(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s) {
@@ -660,7 +643,7 @@ void launch_gather(const CellList& C, const Arrays& src, const Arrays& dst, int 
 
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s) {
-  launch_scatter(C, n, ctr, s);
+  launch_scatter(C, n, ncells, ctr, s);
   launch_cell_sort(C, n, ncells, ctr, s);
   launch_gather(C, src, dst, n, s);
 }

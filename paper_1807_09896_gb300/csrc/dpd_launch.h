@@ -17,19 +17,17 @@ void launch_key(const SysDesc* S, int nsys, const Arrays& A, const CellList& C, 
                 cudaStream_t s);
 // Kernels one launch_integrate enqueues.
 int integrate_kernels(int n, int nsys);
-// Tiles of the cell scan (its published words).
+// Tiles of the cell scan (one block each).
 int scan_blocks(int ncells);
 // Kernels one launch_scan enqueues (one: the scan is a single pass).
 int scan_kernels(int ncells);
-// Exclusive scan of the cell counts into start (and counts cleared).  A look-back that
-// waits too long sets ST_TIMEOUT in the status of systems 0..nsys-1.  stall_tile >= 0
-// is a test hook: that tile publishes nothing, so its successors time out.
-void launch_scan(const CellList& C, int ncells, int n, DevCounters* ctr, int nsys, int stall_tile,
-                 cudaStream_t s);
+// Exclusive scan of the cell counts into start (and counts cleared), from the counts
+// and the tile totals the drift (or launch_key) left; no block waits on another.
+void launch_scan(const CellList& C, int ncells, int n, cudaStream_t s);
 // Reorder into cell order: scatter, per-cell sort, gather (launch_sort = all three).
 void launch_sort(const CellList& C, const Arrays& src, const Arrays& dst, int n, int ncells,
                  DevCounters* ctr, cudaStream_t s);
-void launch_scatter(const CellList& C, int n, DevCounters* ctr, cudaStream_t s);
+void launch_scatter(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s);
 void launch_cell_sort(const CellList& C, int n, int ncells, DevCounters* ctr, cudaStream_t s);
 void launch_gather(const CellList& C, const Arrays& src, const Arrays& dst, int n, cudaStream_t s);
 // Pair force of the given launch shape; launch_force = the pair kernel, then (for

@@ -26,12 +26,12 @@ SETTABLE = {
     "shear_ref": 2.5, "sample_every": 3.0, "a_ff": 20.0, "a_fs": 30.0, "gamma": 3.0, "sigma": 2.0,
     "g_x": 0.01, "g_y": 0.0, "g_z": -0.02, "phase_eps": 0.6, "force_law": 1.0, "S_r_ff": 30.0,
     "S_a_ff": 15.0, "S_r_fs": 60.0, "S_a_fs": 30.0, "r0_r": 0.7, "r0_a": 0.95, "sph_dim": 2.0,
-    "use_graph": 0.0, "graph_steps": 8.0, "force_variant": 2.0, "scan_stall_tile": -1.0,
+    "use_graph": 0.0, "graph_steps": 8.0, "force_variant": 2.0,
 }
 INVALID = {
     "reflect_variant": 2.0, "band_margin": 0.0, "seed": -1.0, "shear_z": 0.1, "shear_axis": 3.0,
     "force_law": 2.0, "r0_r": 1.5, "r0_a": 0.0, "sph_dim": 4.0, "phase_eps": 0.0,
-    "graph_steps": 3.0, "force_variant": 1e6, "gamma": -1.0, "scan_stall_tile": -2.0,
+    "graph_steps": 3.0, "force_variant": 1e6, "gamma": -1.0,
 }
 
 
