@@ -102,6 +102,13 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   // the closing kick reads this particle's velocity after the whole pair loop: start
   // bringing it into L2 now, so that the thread does not end on a DRAM round trip
   asm volatile("prefetch.global.L2 [%0];" ::"l"(A.vel + i));
+  // Candidates are tested against the target shifted once per segment, u = t + s (one
+  // rounding at a periodic seam), with a cut of 1 + 8 ulp(L) on r^2 that covers that
+  // rounding; the pair loop then keeps exactly the pairs whose minimum-image separation
+  // has 0 < r^2 < 1 (which also drops the particle itself).  For every pair inside r_c
+  // that separation equals the segment's bit for bit, so the pairs and their order are
+  // those of an exact test.
+  const float r2cut = fmaf(8.0f * 0x1p-23f, fmaxf(P.L[0], fmaxf(P.L[1], P.L[2])), 1.0f);
 
   float fx = 0.f, fy = 0.f, fz = 0.f;
   int cnt = 0;
@@ -135,35 +142,47 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   int seg = 0;
   uint32_t j = 0, e = 0;
   float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
+  float ux = tx, uy = ty, uz = tz;
+  bool more = true;
   for (;;) {
-    // fill the list with candidates inside r_c until it is full or the cells run out
-    while (cnt < kListCap) {
+    // fill the list with candidates in rounds of up to four while it has room for four
+    while (cnt <= kListCap - 4) {
       if (j == e) {
-        if (seg == nseg) break;
-        const int part = inner ? 1 : seg % 3;
-        const int rowi = inner ? seg : seg / 3;
-        const int dy = rowi % 3 - 1, dz = rowi / 3 - 1;
-        int z = cz + dz, y = cy + dy;
-        tz = pi.z; sz = 0.f; ty = pi.y; sy = 0.f;
-        if (z < 0) { z += ncz; sz = P.L[2]; } else if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
-        if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
-        const int row = (z * ncy + y) * ncx;
+        if (seg == nseg) {
+          more = false;
+          break;
+        }
         if (inner) {
-          j = seg_b[rowi][threadIdx.x];
-          e = seg_e[rowi][threadIdx.x];
-          tx = pi.x; sx = 0.f;
+          // the row's bounds from the table; a shift only where the row wraps in y or z
+          // (the same sums the general path forms: t - L, or t + L)
+          const int y = cy + seg % 3 - 1, z = cz + seg / 3 - 1;
+          j = seg_b[seg][threadIdx.x];
+          e = seg_e[seg][threadIdx.x];
+          ux = pi.x;
+          uy = y < 0 ? pi.y + P.L[1] : (y >= ncy ? pi.y - P.L[1] : pi.y);
+          uz = z < 0 ? pi.z + P.L[2] : (z >= ncz ? pi.z - P.L[2] : pi.z);
         } else {
+          const int part = seg % 3, rowi = seg / 3;
+          const int dy = rowi % 3 - 1, dz = rowi / 3 - 1;
+          int z = cz + dz, y = cy + dy;
+          tz = pi.z; sz = 0.f; ty = pi.y; sy = 0.f;
+          if (z < 0) { z += ncz; sz = P.L[2]; } else if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
+          if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
+          const int row = (z * ncy + y) * ncx;
           int x = cx + part - 1;
           tx = pi.x; sx = 0.f;
           if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
           j = __ldg(&start[row + x]);
           e = __ldg(&start[row + x + 1]);
+          ux = tx + sx;
+          uy = ty + sy;
+          uz = tz + sz;
         }
         ++seg;
-        continue;
+        // the round below takes the new segment's first candidates in the same pass
       }
       // up to four candidates per round, their loads issued together
-      const uint32_t m = min(min(e - j, 4u), (uint32_t)(kListCap - cnt));
+      const uint32_t m = min(e - j, 4u);
       float4 q[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -171,11 +190,11 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (u < (int)m) {
-          const float dx = tx - (q[u].x - sx);
-          const float dy = ty - (q[u].y - sy);
-          const float dz = tz - (q[u].z - sz);
+          const float dx = ux - q[u].x;
+          const float dy = uy - q[u].y;
+          const float dz = uz - q[u].z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 < 1.0f && r2 > 0.0f) list[cnt++][threadIdx.x] = (int)(j + u);
+          if (r2 < r2cut) list[cnt++][threadIdx.x] = (int)(j + u);
         }
       }
       j += m;
@@ -188,12 +207,14 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
       const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
       const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (!(r2 < 1.0f && r2 > 0.0f)) continue;
       const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, is_solid(pj.w), idi, step);
       fx = fmaf(t.x, t.y, fx);
       fy = fmaf(t.x, t.z, fy);
       fz = fmaf(t.x, t.w, fz);
     }
-    if (cnt < kListCap) break;  // the cells ran out before the list filled
+    if (!more) break;  // the cells ran out
     cnt = 0;
   }
 
@@ -240,6 +261,14 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
   const uint32_t idi = id_of(pi.w);
   const float4* __restrict__ pos = A.pos;
   const float4* __restrict__ vt = A.vt;
+  // Candidates are tested against the target shifted once per segment, u = t + s (one
+  // rounding at a periodic seam), with a cut of 1 + 8 ulp(L) on r^2 that covers that
+  // rounding; the pair loop then keeps exactly the pairs whose minimum-image separation
+  // has 0 < r^2 < 1.  For every pair inside r_c that separation equals the segment's
+  // (shift and subtraction are both exact, or one rounding of the exact difference), so
+  // the pairs and their order are those of an exact test.
+  const float r2cut = fmaf(8.0f * 0x1p-23f, fmaxf(P.L[0], fmaxf(P.L[1], P.L[2])), 1.0f);
+  const uint32_t smask = solid_i ? kSolidBit : 0u;  // solid-solid pairs are never listed
   const int cx = cell_coord(pi.x, P.inv_edge[0], P.nc[0]);
   const int cy = cell_coord(pi.y, P.inv_edge[1], P.nc[1]);
   const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
@@ -269,15 +298,31 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
   int cnt = 0, seg = 0;
   uint32_t j = 0, e = 0;
   float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
+  float ux = tx, uy = ty, uz = tz;
+  bool more = true;
   for (;;) {
-    while (cnt < kListCap) {
+    // rounds of up to four candidates while the list has room for four
+    while (cnt <= kListCap - 4) {
       if (j == e) {
-        if (seg == nseg) break;
+        if (seg == nseg) {
+          more = false;
+          break;
+        }
         tx = pi.x; ty = pi.y; tz = pi.z;
         sx = 0.f; sy = 0.f; sz = 0.f;
-        if (inner && seg == 0) {
-          j = seg_b[0][threadIdx.x];
-          e = seg_e[0][threadIdx.x];
+        if (inner) {
+          // the range's bounds from the table; a shift only where a row wraps in y or z
+          // (the same sums the general path forms: t - L, or t + L)
+          j = seg_b[seg][threadIdx.x];
+          e = seg_e[seg][threadIdx.x];
+          if (seg > 0) {
+            int dy, dz;
+            half_row(seg - 1, &dy, &dz);
+            const int y = cy + dy;
+            ty = y < 0 ? pi.y : (y >= ncy ? pi.y - P.L[1] : pi.y);
+            sy = y < 0 ? P.L[1] : 0.f;
+            tz = cz + dz >= ncz ? pi.z - P.L[2] : pi.z;
+          }
         } else if (seg == 0) {
           j = (uint32_t)i + 1u;
           e = __ldg(&start[own_row + cx + 1]);
@@ -287,27 +332,26 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
           j = __ldg(&start[own_row + x]);
           e = __ldg(&start[own_row + x + 1]);
         } else {
-          const int r = inner ? seg - 1 : (seg - 2) / 3;
           int dy, dz;
-          half_row(r, &dy, &dz);
+          half_row((seg - 2) / 3, &dy, &dz);
           int z = cz + dz, y = cy + dy;
           if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
           if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
           const int row = (z * ncy + y) * ncx;
-          if (inner) {
-            j = seg_b[seg][threadIdx.x];
-            e = seg_e[seg][threadIdx.x];
-          } else {
-            int x = cx + (seg - 2) % 3 - 1;
-            if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
-            j = __ldg(&start[row + x]);
-            e = __ldg(&start[row + x + 1]);
-          }
+          int x = cx + (seg - 2) % 3 - 1;
+          if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
+          j = __ldg(&start[row + x]);
+          e = __ldg(&start[row + x + 1]);
         }
+        ux = tx + sx;
+        uy = ty + sy;
+        uz = tz + sz;
         ++seg;
-        continue;
+        // the round below takes the new segment's first candidates in the same pass
+        // (none if it is empty): lanes that change segments then cost the warp the
+        // switch, not a whole extra pass of rounds for the others
       }
-      const uint32_t m = min(min(e - j, 4u), (uint32_t)(kListCap - cnt));
+      const uint32_t m = min(e - j, 4u);
       float4 q[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -315,12 +359,11 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (u < (int)m) {
-          const float dx = tx - (q[u].x - sx);
-          const float dy = ty - (q[u].y - sy);
-          const float dz = tz - (q[u].z - sz);
+          const float dx = ux - q[u].x;
+          const float dy = uy - q[u].y;
+          const float dz = uz - q[u].z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 < 1.0f && r2 > 0.0f && !(solid_i && is_solid(q[u].w)))
-            list[cnt++][threadIdx.x] = (int)(j + u);
+          if (r2 < r2cut && (tag_of(q[u].w) & smask) == 0u) list[cnt++][threadIdx.x] = (int)(j + u);
         }
       }
       j += m;
@@ -332,6 +375,8 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
       const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
       const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
       const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (!(r2 < 1.0f && r2 > 0.0f)) continue;
       const bool solid_j = is_solid(pj.w);
       const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, solid_i || solid_j, idi, step);
       const float gx = t.x * t.y, gy = t.x * t.z, gz = t.x * t.w;
@@ -344,7 +389,7 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
         fix_add(&facc[2 * stride + jj], -gz);
       }
     }
-    if (cnt < kListCap) break;  // the cells ran out before the list filled
+    if (!more) break;  // the cells ran out
     cnt = 0;
   }
   // the own share goes to frc without an atomic (nothing else writes it): whoever reads
