@@ -105,7 +105,7 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   // Candidates are tested against the target shifted once per segment, u = t + s (one
   // rounding at a periodic seam), with a cut of 1 + 8 ulp(L) on r^2 that covers that
   // rounding; the pair loop then keeps exactly the pairs whose minimum-image separation
-  // has 0 < r^2 < 1 (which also drops the particle itself).  For every pair inside r_c
+  // has 0 < r^2 < 1.  For every pair inside r_c
   // that separation equals the segment's bit for bit, so the pairs and their order are
   // those of an exact test.
   const float r2cut = fmaf(8.0f * 0x1p-23f, fmaxf(P.L[0], fmaxf(P.L[1], P.L[2])), 1.0f);
@@ -183,19 +183,21 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       }
       // up to four candidates per round, their loads issued together
       const uint32_t m = min(e - j, 4u);
+      if (m == 0u) continue;  // an empty segment: on to the next
+      // slots past the segment's end re-read its last candidate (in range) and never count
       float4 q[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (u < (int)m) q[u] = __ldg(&pos[j + u]);
+      for (int u = 0; u < 4; ++u) q[u] = __ldg(&pos[min(j + (uint32_t)u, e - 1u)]);
+      // branch-free append: every slot is written, the count moves only on a hit (the
+      // round starts with room for four, so the writes stay inside the list)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (u < (int)m) {
-          const float dx = ux - q[u].x;
-          const float dy = uy - q[u].y;
-          const float dz = uz - q[u].z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 < r2cut) list[cnt++][threadIdx.x] = (int)(j + u);
-        }
+        const float dx = ux - q[u].x;
+        const float dy = uy - q[u].y;
+        const float dz = uz - q[u].z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        list[cnt][threadIdx.x] = (int)(j + u);
+        cnt += (u < (int)m) & (r2 < r2cut) & (r2 > 0.0f);  // r2 = 0: the particle itself
       }
       j += m;
     }
@@ -352,19 +354,21 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
         // switch, not a whole extra pass of rounds for the others
       }
       const uint32_t m = min(e - j, 4u);
+      if (m == 0u) continue;  // an empty segment: on to the next
+      // slots past the segment's end re-read its last candidate (in range) and never count
       float4 q[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (u < (int)m) q[u] = __ldg(&pos[j + u]);
+      for (int u = 0; u < 4; ++u) q[u] = __ldg(&pos[min(j + (uint32_t)u, e - 1u)]);
+      // branch-free append: every slot is written, the count moves only on a hit (the
+      // round starts with room for four, so the writes stay inside the list)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (u < (int)m) {
-          const float dx = ux - q[u].x;
-          const float dy = uy - q[u].y;
-          const float dz = uz - q[u].z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 < r2cut && (tag_of(q[u].w) & smask) == 0u) list[cnt++][threadIdx.x] = (int)(j + u);
-        }
+        const float dx = ux - q[u].x;
+        const float dy = uy - q[u].y;
+        const float dz = uz - q[u].z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        list[cnt][threadIdx.x] = (int)(j + u);
+        cnt += (u < (int)m) & (r2 < r2cut) & ((tag_of(q[u].w) & smask) == 0u);
       }
       j += m;
     }
