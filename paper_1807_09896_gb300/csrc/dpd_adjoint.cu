@@ -147,18 +147,19 @@ __device__ __forceinline__ float phi_and_grad(const StepParams& P, float x, floa
 // shuffles.  The calibration windows are small (tens of thousands of particles), where
 // one thread per target left ~5 warps per SM and the kernel waited on its loads.
 constexpr int kAdjLanes = 4;
+constexpr int kAdjList = 16;  // listed pairs per lane between evaluations
 
 __global__ void __launch_bounds__(128)
 k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restrict__ vt,
             const uint32_t* __restrict__ start, int n, uint32_t step, const float4* __restrict__ rbar,
             const float4* __restrict__ vbar, const float4* __restrict__ fbar, float4* Rb, float4* Vb,
             float tie_coef, double* tpart) {
+  __shared__ int alist[kAdjList][128];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / kAdjLanes, sub = t % kAdjLanes;
   double ta = 0.0, tg = 0.0;
   float Rx = 0.f, Ry = 0.f, Rz = 0.f, Ux = 0.f, Uy = 0.f, Uz = 0.f;
   bool target = false;
-  // cell starts left by a timed-out scan are not a valid prefix (the status reports it)
   if (i < n) {
     const float4 pi = pos[i];
     target = !is_solid(pi.w);
@@ -177,58 +178,110 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
       const int cx = cell_coord(pi.x, P.inv_edge[0], P.nc[0]);
       const int cy = cell_coord(pi.y, P.inv_edge[1], P.nc[1]);
       const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
+      const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
+      // This lane's plane dz of the 27 cells, in the order dy, then dx, then each cell's
+      // particles: rows of three cells are one range away from the x seam, single cells
+      // on it.  Candidates are tested in rounds of four against the target shifted once
+      // per range (a cut of 1 + 8 ulp(L) on r^2 covers that rounding) into a list; the
+      // listed pairs are then evaluated in order with the exact minimum-image test, so
+      // the pairs and the order of every sum are those of a cell-by-cell walk.
+      const float r2cut = fmaf(8.0f * 0x1p-23f, fmaxf(P.L[0], fmaxf(P.L[1], P.L[2])), 1.0f);
       const int dz = sub - 1;
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x = wrap_node(cx + dx, P.nc[0]), y = wrap_node(cy + dy, P.nc[1]),
-                    z = wrap_node(cz + dz, P.nc[2]);
-          const int c = (z * P.nc[1] + y) * P.nc[0] + x;
-          for (uint32_t j = start[c]; j < start[c + 1]; ++j) {
-            const float4 pj = pos[j];
-            const float ddx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
-            const float ddy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
-            const float ddz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
-            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-            if (!(r2 < 1.0f && r2 > 0.0f)) continue;
-            const float inv_r = rsqrtf(r2);
-            const float r = r2 * inv_r;
-            const float w = 1.0f - r;
-            const float ex = ddx * inv_r, ey = ddy * inv_r, ez = ddz * inv_r;
-            const bool solid_j = is_solid(pj.w);
-            float ujx, ujy, ujz, a, Gx = Fx, Gy = Fy, Gz = Fz;
-            if (solid_j) {
-              ujx = P.vw[0]; ujy = P.vw[1]; ujz = P.vw[2];
-              a = P.a_fs;
-            } else {
-              const float4 vtj = vt[j];
-              ujx = vtj.x; ujy = vtj.y; ujz = vtj.z;
-              a = P.a_ff;
-              const float4 fbj = fbar[j], vbj = vbar[j];
-              const float kick_j = vtj.w == 0.0f ? P.half_dt : 0.0f;
-              Gx -= fbj.x + kick_j * vbj.x;
-              Gy -= fbj.y + kick_j * vbj.y;
-              Gz -= fbj.z + kick_j * vbj.z;
+      const int z = wrap_node(cz + dz, ncz);
+      const float uz = cz + dz < 0 ? pi.z + P.L[2] : (cz + dz >= ncz ? pi.z - P.L[2] : pi.z);
+      const bool inner = cx > 0 && cx < ncx - 1;
+      const int nseg = inner ? 3 : 9;
+      int seg = 0, cnt = 0;
+      uint32_t j = 0, e = 0;
+      float ux = pi.x, uy = pi.y;
+      bool more = true;
+      for (;;) {
+        while (cnt <= kAdjList - 4) {
+          if (j == e) {
+            if (seg == nseg) {
+              more = false;
+              break;
             }
-            const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
-            const float eu = ex * ux + ey * uy + ez * uz;
-            const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.seed_lo, P.seed_hi);
-            const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
-            const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
-            const float eG = ex * Gx + ey * Gy + ez * Gz;
-            const float gw2 = P.gamma * w * w;
-            const float cu = -gw2 * eG * inv_r;
-            const float cm = m * inv_r;
-            Rx += m_r * eG * ex + cu * (ux - eu * ex) + cm * (Gx - eG * ex);
-            Ry += m_r * eG * ey + cu * (uy - eu * ey) + cm * (Gy - eG * ey);
-            Rz += m_r * eG * ez + cu * (uz - eu * ez) + cm * (Gz - eG * ez);
-            Ux -= gw2 * eG * ex;
-            Uy -= gw2 * eG * ey;
-            Uz -= gw2 * eG * ez;
-            const float eF = ex * Fx + ey * Fy + ez * Fz;
-            if (solid_j) ta += (double)(w * eF);
-            tg += (double)((-w * w * eu + tie_coef * w * xi) * eF);
+            const int dy = (inner ? seg : seg / 3) - 1;
+            const int y = wrap_node(cy + dy, ncy);
+            uy = cy + dy < 0 ? pi.y + P.L[1] : (cy + dy >= ncy ? pi.y - P.L[1] : pi.y);
+            const int row = (z * ncy + y) * ncx;
+            if (inner) {
+              j = start[row + cx - 1];
+              e = start[row + cx + 2];
+              ux = pi.x;
+            } else {
+              const int dx = seg % 3 - 1;
+              const int x = wrap_node(cx + dx, ncx);
+              ux = cx + dx < 0 ? pi.x + P.L[0] : (cx + dx >= ncx ? pi.x - P.L[0] : pi.x);
+              j = start[row + x];
+              e = start[row + x + 1];
+            }
+            ++seg;
           }
+          const uint32_t m = min(e - j, 4u);
+          if (m == 0u) continue;
+          float4 q[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) q[u] = pos[min(j + (uint32_t)u, e - 1u)];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float ddx = ux - q[u].x, ddy = uy - q[u].y, ddz = uz - q[u].z;
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            alist[cnt][threadIdx.x] = (int)(j + u);
+            cnt += (u < (int)m) & (r2 < r2cut) & (r2 > 0.0f);
+          }
+          j += m;
         }
+        for (int k = 0; k < cnt; ++k) {
+          const uint32_t j = (uint32_t)alist[k][threadIdx.x];
+          const float4 pj = pos[j];
+          const float ddx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
+          const float ddy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
+          const float ddz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+          const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+          if (!(r2 < 1.0f && r2 > 0.0f)) continue;
+        const float inv_r = rsqrtf(r2);
+        const float r = r2 * inv_r;
+        const float w = 1.0f - r;
+        const float ex = ddx * inv_r, ey = ddy * inv_r, ez = ddz * inv_r;
+        const bool solid_j = is_solid(pj.w);
+        float ujx, ujy, ujz, a, Gx = Fx, Gy = Fy, Gz = Fz;
+        if (solid_j) {
+          ujx = P.vw[0]; ujy = P.vw[1]; ujz = P.vw[2];
+          a = P.a_fs;
+        } else {
+          const float4 vtj = vt[j];
+          ujx = vtj.x; ujy = vtj.y; ujz = vtj.z;
+          a = P.a_ff;
+          const float4 fbj = fbar[j], vbj = vbar[j];
+          const float kick_j = vtj.w == 0.0f ? P.half_dt : 0.0f;
+          Gx -= fbj.x + kick_j * vbj.x;
+          Gy -= fbj.y + kick_j * vbj.y;
+          Gz -= fbj.z + kick_j * vbj.z;
+        }
+        const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
+        const float eu = ex * ux + ey * uy + ez * uz;
+        const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.seed_lo, P.seed_hi);
+        const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
+        const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
+        const float eG = ex * Gx + ey * Gy + ez * Gz;
+        const float gw2 = P.gamma * w * w;
+        const float cu = -gw2 * eG * inv_r;
+        const float cm = m * inv_r;
+        Rx += m_r * eG * ex + cu * (ux - eu * ex) + cm * (Gx - eG * ex);
+        Ry += m_r * eG * ey + cu * (uy - eu * ey) + cm * (Gy - eG * ey);
+        Rz += m_r * eG * ez + cu * (uz - eu * ez) + cm * (Gz - eG * ez);
+        Ux -= gw2 * eG * ex;
+        Uy -= gw2 * eG * ey;
+        Uz -= gw2 * eG * ez;
+        const float eF = ex * Fx + ey * Fy + ez * Fz;
+        if (solid_j) ta += (double)(w * eF);
+        tg += (double)((-w * w * eu + tie_coef * w * xi) * eF);
+        }
+        if (!more) break;
+        cnt = 0;
+      }
     }
   }
   // the target's four lanes are adjacent: add their sums (every lane takes part)
