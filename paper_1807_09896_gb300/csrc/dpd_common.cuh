@@ -122,8 +122,13 @@ __device__ __forceinline__ int sys_of(const SysDesc* __restrict__ S, int nsys, u
   return lo;
 }
 
+// Readable slots past the last particle in the position arrays: a candidate round of
+// the force kernels loads four consecutive positions from one address, and the slots
+// past a range's end (at most three) never count.
+constexpr int kPosPad = 4;
+
 struct Arrays {
-  float4* pos;
+  float4* pos;  // n + kPosPad slots in the step's buffers
   float4* vt;
   float4* vel;  // .w: 1 if the particle was reflected in the step that produced it
   float4* frc;

@@ -110,7 +110,7 @@ int engine_reserve(Engine& E, int nsys, int n, int ncells) {
     engine_free_graphs(E);
     free_particle_buffers(E);
     for (auto& A : E.arr) {
-      ECU(E, dev_alloc(&A.pos, n));
+      ECU(E, dev_alloc(&A.pos, (size_t)n + kPosPad));
       ECU(E, dev_alloc(&A.vt, n));
       ECU(E, dev_alloc(&A.vel, n));
       ECU(E, dev_alloc(&A.frc, n));

@@ -184,10 +184,12 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       // up to four candidates per round, their loads issued together
       const uint32_t m = min(e - j, 4u);
       if (m == 0u) continue;  // an empty segment: on to the next
-      // slots past the segment's end re-read its last candidate (in range) and never count
+      // four consecutive slots from one address (the arrays carry kPosPad readable slots
+      // past the last particle); those past the segment's end never count
       float4 q[4];
+      const float4* __restrict__ pj0 = pos + j;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) q[u] = __ldg(&pos[min(j + (uint32_t)u, e - 1u)]);
+      for (int u = 0; u < 4; ++u) q[u] = __ldg(pj0 + u);
       // branch-free append: every slot is written, the count moves only on a hit (the
       // round starts with room for four, so the writes stay inside the list)
 #pragma unroll
@@ -355,10 +357,12 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
       }
       const uint32_t m = min(e - j, 4u);
       if (m == 0u) continue;  // an empty segment: on to the next
-      // slots past the segment's end re-read its last candidate (in range) and never count
+      // four consecutive slots from one address (the arrays carry kPosPad readable slots
+      // past the last particle); those past the segment's end never count
       float4 q[4];
+      const float4* __restrict__ pj0 = pos + j;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) q[u] = __ldg(&pos[min(j + (uint32_t)u, e - 1u)]);
+      for (int u = 0; u < 4; ++u) q[u] = __ldg(pj0 + u);
       // branch-free append: every slot is written, the count moves only on a hit (the
       // round starts with room for four, so the writes stay inside the list)
 #pragma unroll
