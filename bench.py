@@ -47,23 +47,24 @@ PHASE_FIELD_BYTES_PER_NODE = 8
 # At rho = 3 with unit cells there are 81 candidates and 4/3 pi rho = 12.57 pairs.
 OPS_PER_CANDIDATE = 13
 OPS_PER_PAIR = 115
-# Algorithmic HBM bytes per particle and step of the whole step: integrate 104,
-# scan 5, scatter 12, per-cell order 9, gather 100, force 80 (design notes).
-BYTES_PER_PARTICLE_STEP = 310
+# Algorithmic HBM bytes per particle and step of the whole step: integrate 100,
+# scan 5, scatter 11, per-cell order 12, gather 100, force 80 (design notes).
+BYTES_PER_PARTICLE_STEP = 308
 # Algorithmic bytes of each phase's kernel(s), per fluid particle, per solid
 # particle and per cell (minimal traffic: every array the kernel must read or write,
-# once).  integrate: pos, vel, frc in; pos, vel, vt, key, rank out (a resting solid
-# particle: pos in, key and rank out); after a half-shell force the 24 B of
+# once).  integrate: pos, vel, frc in; pos, vel, vt, key out (a resting solid
+# particle: pos in, key out); after a half-shell force the 24 B of
 # fixed-point sums replace frc and are cleared (+32 B).  scan: count read twice,
-# start written, count cleared.  scatter: key, rank, start in; perm out.  cell_sort:
-# perm in and out, start in.  gather: perm, then pos, vt, vel in and out.
+# start written, and written again into count as the scatter's slot cursor.  scatter:
+# key in, perm out, each cell's cursor read and written.  cell_sort: perm in and out,
+# start in, count zeroed.  gather: perm, then pos, vt, vel in and out.
 # force_pairs: full shell pos, vt, vel in, frc and vel out; half shell pos, vt in and
 # 24 B of fixed-point sums.  (A step launches no finish pass: the drift does its work.)
 PHASE_BYTES = {
-    "integrate": {False: (104, 24, 0), True: (136, 24, 0)},
+    "integrate": {False: (100, 20, 0), True: (132, 20, 0)},
     "scan": (0, 0, 16),
-    "scatter": (12, 12, 4),
-    "cell_sort": (8, 8, 8),
+    "scatter": (8, 8, 8),
+    "cell_sort": (8, 8, 12),
     "gather": (100, 100, 0),
     "force_pairs": {False: (80, 16, 0), True: (56, 32, 0)},
 }

@@ -136,8 +136,8 @@ struct Arrays {
 
 struct CellList {
   uint32_t* key;    // cell of each particle (current order)
-  uint32_t* rank;   // arrival slot inside its cell (atomic order)
-  uint32_t* count;  // particles per cell (zeroed by the scan)
+  uint32_t* count;  // particles per cell; after the scan the cell's next free slot (the
+                    // scatter's cursor); zeroed by the per-cell sort
   uint32_t* start;  // exclusive prefix of count, ncells + 1 entries
   uint32_t* perm;   // new position -> old position
   // the scan's tiles of kScanTileCells cells: the particles each tile's cells hold,

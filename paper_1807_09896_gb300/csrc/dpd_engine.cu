@@ -50,10 +50,9 @@ static void free_particle_buffers(Engine& E) {
     A = Arrays{};
   }
   cudaFree(E.cl.key);
-  cudaFree(E.cl.rank);
   cudaFree(E.cl.perm);
   cudaFree(E.facc);
-  E.cl.key = E.cl.rank = E.cl.perm = nullptr;
+  E.cl.key = E.cl.perm = nullptr;
   E.facc = nullptr;
   E.cap = 0;
 }
@@ -116,7 +115,6 @@ int engine_reserve(Engine& E, int nsys, int n, int ncells) {
       ECU(E, dev_alloc(&A.frc, n));
     }
     ECU(E, dev_alloc(&E.cl.key, n));
-    ECU(E, dev_alloc(&E.cl.rank, n));
     ECU(E, dev_alloc(&E.cl.perm, n));
     ECU(E, dev_alloc(&E.facc, 3 * (size_t)n));
     ECU(E, cudaMemsetAsync(E.facc, 0, sizeof(unsigned long long) * 3 * (size_t)n, E.stream));

@@ -146,19 +146,14 @@ __device__ __forceinline__ void integrate_body(const StepParams& P, uint32_t cel
   }
   const uint32_t c = cell_off + (uint32_t)cell_of(P, p.x, p.y, p.z);
   C.key[i] = c;
-  // Arrival slot in the cell.  Neighbouring threads mostly hold particles of the same
-  // cell (the arrays are in cell order from the previous step), so the lanes of a warp
-  // that share a cell take their slots with one atomic: the group's lowest lane adds
-  // the group size and each lane takes base + its rank in the group.  (The per-cell id
-  // order of the sort fixes the final order, so the slots' order does not matter.)
+  // The cell's count.  Neighbouring threads mostly hold particles of the same cell (the
+  // arrays are in cell order from the previous step), so the lanes of a warp that share
+  // a cell add to it with one atomic, whose result nobody waits for; the scatter takes
+  // the slots (the per-cell order of the sort fixes the final order).
   const unsigned active = __activemask();
   const unsigned peers = __match_any_sync(active, c);
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&C.count[c], (uint32_t)__popc(peers));
-  base = __shfl_sync(active, base, leader);
-  C.rank[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  if (lane == __ffs(peers) - 1) atomicAdd(&C.count[c], (uint32_t)__popc(peers));
   // the scan's tile totals, one atomic per tile the warp touches (usually one)
   const uint32_t tl = c / (uint32_t)kScanTileCells;
   const int first = __ffs(active) - 1;
@@ -207,7 +202,7 @@ __global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellLis
   const float4 p = A.pos[i];
   const uint32_t c = S[sk].cell_off + (uint32_t)cell_of(S[sk].P, p.x, p.y, p.z);
   C.key[i] = (uint32_t)c;
-  C.rank[i] = atomicAdd(&C.count[c], 1u);
+  atomicAdd(&C.count[c], 1u);
   atomicAdd(tile_counter(C.tile_total, c / (uint32_t)kScanTileCells, i >> 5), 1u);
 }
 
@@ -220,8 +215,9 @@ __global__ void k_key(const SysDesc* __restrict__ S, int nsys, Arrays A, CellLis
 // decoupled look-back (Merrill and Garland 2016) has to learn the same sum from its
 // predecessors' published words while they run; on GB300 its chain of release
 // stores and acquire polls took 11-13 us for the 340k cells of the 1M-particle
-// channel whatever the tile shape.  The scan zeroes the counts for the next step and
-// the scatter, which follows every scan, zeroes the tile totals.
+// channel whatever the tile shape.  The scan leaves each cell's start in its count,
+// where the scatter takes the cell's slots; the per-cell sort zeroes the counts for the
+// next step, and the scatter, which follows every scan, zeroes the tile totals.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 8;
@@ -307,14 +303,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(uint32_t* count, int m, u
       q.w = q.z + v[k + 2];
       run = q.w + v[k + 3];
       *reinterpret_cast<uint4*>(start + base + k) = q;
-      *reinterpret_cast<uint4*>(count + base + k) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(count + base + k) = q;
     }
   } else {
 #pragma unroll
     for (int k = 0; k < kScanPerThread; ++k) {
       if (base + k < m) {
         start[base + k] = run;
-        count[base + k] = 0u;
+        count[base + k] = run;
       }
       run += v[k];
     }
@@ -332,7 +328,7 @@ __global__ void k_scatter(CellList C, int n, int ntw, DevCounters* ctr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   for (int q = i; q < ntw; q += gridDim.x * blockDim.x) C.tile_total[(size_t)q * kTileStride] = 0u;
   if (i >= n) return;
-  const uint32_t d = C.start[C.key[i]] + C.rank[i];
+  const uint32_t d = atomicAdd(&C.count[C.key[i]], 1u);  // the cell's next slot
   if (d < (uint32_t)n)
     C.perm[d] = (uint32_t)i;
   else
@@ -350,6 +346,7 @@ constexpr int kCellSortCap = 48;
 __global__ void k_cell_sort(CellList C, int ncells, int n, DevCounters* ctr) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
+  C.count[c] = 0u;  // the scatter's slot cursor: zero for the next step's counts
   const uint32_t b = C.start[c], e = C.start[c + 1];
   if (b > e || e > (uint32_t)n) {  // starts not a valid prefix (only after a failed scan)
     atomicOr(&ctr->status, ST_OVERFLOW);
