@@ -262,7 +262,7 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
         }
         const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
         const float eu = ex * ux + ey * uy + ez * uz;
-        const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.seed_lo, P.seed_hi);
+        const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.rkey);
         const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
         const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
         const float eG = ex * Gx + ey * Gy + ez * Gz;

@@ -66,6 +66,10 @@ StepParams make_params(const dpd_system* h) {
   P.sigma_rsqdt = (float)(h->sigma / std::sqrt(h->dt));
   P.seed_lo = (uint32_t)(h->seed & 0xffffffffu);
   P.seed_hi = (uint32_t)(h->seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // the noise's Philox round keys
+    P.rkey[2 * r] = P.seed_lo + (uint32_t)r * 0x9E3779B9u;
+    P.rkey[2 * r + 1] = P.seed_hi + (uint32_t)r * 0xBB67AE85u;
+  }
   P.sys = h->sys;
   P.reflect_variant = h->reflect_variant;
   P.margin = (float)h->margin;

@@ -73,6 +73,10 @@ struct StepParams {
   int moving;    // vw or sh nonzero: the solid moves
   float a_ff, a_fs, gamma, sigma_rsqdt;
   uint32_t seed_lo, seed_hi, sys;
+  // Philox4x32-10 round keys of the pair noise, (seed_lo + r 0x9E3779B9, seed_hi +
+  // r 0xBB67AE85) for round r = 0..9: the key schedule depends on the seed alone, so it
+  // is formed once on the host (single-system kernels read it from the parameter bank)
+  uint32_t rkey[20];
   int reflect_variant;
   float margin;
   const float* phi;   // phase-field nodes, x fastest (nullptr: phi = +1)
@@ -244,9 +248,18 @@ __device__ __forceinline__ float philox_u01(uint32_t w) {
 }
 
 __device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t step, uint32_t sys,
-                                            uint32_t k0, uint32_t k1) {
+                                            const uint32_t (&rkey)[20]) {
   uint32_t c0 = min(ida, idb), c1 = max(ida, idb), c2 = step, c3 = sys;
-  philox4x32_10(c0, c1, c2, c3, k0, k1);
+  // Philox4x32-10 rounds with the precomputed keys (the same rounds as philox4x32_10)
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ rkey[2 * round];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ rkey[2 * round + 1];
+    c3 = lo0;
+  }
   const float u0 = (__uint2float_rn(c0 >> 9) + 0.5f) * 0x1p-23f;
   const float u1 = (__uint2float_rn(c1 >> 9) + 0.5f) * 0x1p-23f;
   // cos(2 pi u1) = -cos(2 pi u1 - pi), evaluated by the hardware cosine on an

@@ -57,14 +57,14 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
   if constexpr (kLaw == 0) {
     const float a = solid_pair ? P.a_fs : P.a_ff;
     const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
-    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
+    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.rkey);
     return make_float4(w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi), ex, ey, ez);
   } else {
     const float kr = solid_pair ? P.sph_kr_fs : P.sph_kr_ff;
     const float ka = solid_pair ? P.sph_ka_fs : P.sph_ka_ff;
     const float c = kr * spline_slope(r * P.sph_ihr) - ka * spline_slope(r * P.sph_iha);
     const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
-    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
+    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.rkey);
     return make_float4(fmaf(w, P.sigma_rsqdt * xi - P.gamma * w * ev, c), ex, ey, ez);
   }
 }
