@@ -126,6 +126,13 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
   const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
   const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
   const bool inner = cx > 0 && cx < ncx - 1;
+  // Axes on which some lane of the warp has a row or cell across the periodic seam.
+  // Elsewhere a listed pair's minimum-image separation is the plain difference (the
+  // pair is within 1.00005 r_c < L / 2), so the pair loop skips the image test there.
+  const unsigned wm = __activemask();
+  const bool wrap_x = __any_sync(wm, !inner);
+  const bool wrap_y = __any_sync(wm, cy == 0 || cy == ncy - 1);
+  const bool wrap_z = __any_sync(wm, cz == 0 || cz == ncz - 1);
   const int nseg = inner ? 9 : 27;
   if (inner) {
     // the nine row ranges' cell starts, loaded together up front
@@ -208,9 +215,9 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
     for (int k = 0; k < cnt; ++k) {
       const int jj = list[k][threadIdx.x];
       const float4 pj = __ldg(&pos[jj]);
-      const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
-      const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
-      const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+      const float dx = wrap_x ? min_image(pi.x, pj.x, P.L[0], P.halfL[0]) : pi.x - pj.x;
+      const float dy = wrap_y ? min_image(pi.y, pj.y, P.L[1], P.halfL[1]) : pi.y - pj.y;
+      const float dz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (!(r2 < 1.0f && r2 > 0.0f)) continue;
       const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, is_solid(pj.w), idi, step);
@@ -278,6 +285,14 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
   const int cz = cell_coord(pi.z, P.inv_edge[2], P.nc[2]);
   const int ncx = P.nc[0], ncy = P.nc[1], ncz = P.nc[2];
   const bool inner = cx < ncx - 1 && cx > 0;
+  // Axes on which some lane of the warp has a range across the periodic seam (the half
+  // shell looks at z + 1 only).  Elsewhere a listed pair's minimum-image separation is
+  // the plain difference (the pair is within 1.00005 r_c < L / 2), so the pair loop
+  // skips the image test there.
+  const unsigned wm = __activemask();
+  const bool wrap_x = __any_sync(wm, !inner);
+  const bool wrap_y = __any_sync(wm, cy == 0 || cy == ncy - 1);
+  const bool wrap_z = __any_sync(wm, cz == ncz - 1);
   // inner: own tail + next cell (contiguous), then 4 rows of 3 cells; on the x seam:
   // own tail, next cell, then the 12 row cells one by one
   const int nseg = inner ? 5 : 14;
@@ -380,9 +395,9 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
     for (int k = 0; k < cnt; ++k) {
       const int jj = list[k][threadIdx.x];
       const float4 pj = __ldg(&pos[jj]);
-      const float dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
-      const float dy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
-      const float dz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+      const float dx = wrap_x ? min_image(pi.x, pj.x, P.L[0], P.halfL[0]) : pi.x - pj.x;
+      const float dy = wrap_y ? min_image(pi.y, pj.y, P.L[1], P.halfL[1]) : pi.y - pj.y;
+      const float dz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (!(r2 < 1.0f && r2 > 0.0f)) continue;
       const bool solid_j = is_solid(pj.w);
