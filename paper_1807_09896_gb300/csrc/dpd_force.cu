@@ -432,10 +432,11 @@ k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   __shared__ int list[kListCap][kForceThreads];
   __shared__ uint32_t seg_b[5][kForceThreads], seg_e[5][kForceThreads];
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  int sk = 0;
+  if constexpr (kBatch) sk = sys_of_block(S, nsys, (uint32_t)i, blockIdx.x * kForceThreads);
   if (i >= n) return;
   const float4 pi = A.pos[i];
   if constexpr (kBatch) {
-    const int sk = sys_of(S, nsys, (uint32_t)i);
     force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, A,
                                                           facc, (size_t)n, i, pi, ctrs + sk, list,
                                                           seg_b, seg_e);
@@ -484,6 +485,8 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   __shared__ int list[kListCap][kForceThreads];
   __shared__ uint32_t seg_b[9][kForceThreads], seg_e[9][kForceThreads];
   const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  int sk = 0;
+  if constexpr (kBatch) sk = sys_of_block(S, nsys, (uint32_t)i, blockIdx.x * kForceThreads);
   if (i >= n) return;
   const float4 pi = A.pos[i];
   if (is_solid(pi.w)) {  // solid particles feel no force (the reorder does not carry it)
@@ -491,7 +494,6 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
     return;
   }
   if constexpr (kBatch) {
-    const int sk = sys_of(S, nsys, (uint32_t)i);
     force_body<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,
                                                        A, i, pi, list, seg_b, seg_e, kick);
   } else {
