@@ -190,6 +190,12 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
       const int z = wrap_node(cz + dz, ncz);
       const float uz = cz + dz < 0 ? pi.z + P.L[2] : (cz + dz >= ncz ? pi.z - P.L[2] : pi.z);
       const bool inner = cx > 0 && cx < ncx - 1;
+      // axes on which some active lane has a range across the periodic seam; elsewhere
+      // a listed pair's minimum-image separation is the plain difference
+      const unsigned wm = __activemask();
+      const bool wrap_x = __any_sync(wm, !inner);
+      const bool wrap_y = __any_sync(wm, cy == 0 || cy == ncy - 1);
+      const bool wrap_z = __any_sync(wm, cz + dz < 0 || cz + dz >= ncz);
       const int nseg = inner ? 3 : 9;
       int seg = 0, cnt = 0;
       uint32_t j = 0, e = 0;
@@ -236,9 +242,9 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
         for (int k = 0; k < cnt; ++k) {
           const uint32_t j = (uint32_t)alist[k][threadIdx.x];
           const float4 pj = pos[j];
-          const float ddx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
-          const float ddy = min_image(pi.y, pj.y, P.L[1], P.halfL[1]);
-          const float ddz = min_image(pi.z, pj.z, P.L[2], P.halfL[2]);
+          const float ddx = wrap_x ? min_image(pi.x, pj.x, P.L[0], P.halfL[0]) : pi.x - pj.x;
+          const float ddy = wrap_y ? min_image(pi.y, pj.y, P.L[1], P.halfL[1]) : pi.y - pj.y;
+          const float ddz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
           const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
           if (!(r2 < 1.0f && r2 > 0.0f)) continue;
         const float inv_r = rsqrtf(r2);
