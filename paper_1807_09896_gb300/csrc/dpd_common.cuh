@@ -286,6 +286,23 @@ __device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t
   return -(x * rsqrtf(x)) * c;
 }
 
+// The same with the round keys formed on the fly (kernels that read their parameters
+// from global memory, where loading the table costs more than two adds per round).
+__device__ __forceinline__ float pair_noise(uint32_t ida, uint32_t idb, uint32_t step, uint32_t sys,
+                                            uint32_t k0, uint32_t k1) {
+  uint32_t c0 = min(ida, idb), c1 = max(ida, idb), c2 = step, c3 = sys;
+  philox4x32_10(c0, c1, c2, c3, k0, k1);
+  const float u0 = (__uint2float_rn(c0 >> 9) + 0.5f) * 0x1p-23f;
+  const float u1 = (__uint2float_rn(c1 >> 9) + 0.5f) * 0x1p-23f;
+  // cos(2 pi u1) = -cos(2 pi u1 - pi), evaluated by the hardware cosine on an
+  // argument in (-pi, pi), where its absolute error is below 4e-7; the square root
+  // as x * rsqrt(x) (x = -2 ln u0 >= 2.4e-7 > 0).  The logarithm stays the
+  // accurate one: near u0 = 1 its value is tiny and needs full relative accuracy.
+  const float x = -2.0f * logf(u0);
+  const float c = __cosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f));
+  return -(x * rsqrtf(x)) * c;
+}
+
 // Minimum-image separation xi - xj of two coordinates in [0, L).  When the pair
 // straddles the periodic seam the operand near L is shifted by -L first; that
 // shift is exact (Sterbenz: the operand lies in [L/2, L)), so the separation is

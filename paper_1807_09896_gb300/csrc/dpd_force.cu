@@ -42,8 +42,10 @@ __device__ __forceinline__ float spline_slope(float v) {
 //   m = C(r) - gamma w^2 (e . (vt_i - vt_j)) + sigma w xi_ij / sqrt(dt),
 // C(r) = a_ij w for force law 0 (Eq. 4) and C(r) = -dE/dr of Eq. 22 for law 1
 // (Eq. 24).  Every force kernel evaluates pairs through this function, so they agree
-// bit for bit.
-template <int kLaw>
+// bit for bit.  kKeyTable: the noise's Philox round keys come from P.rkey (free in the
+// kernel-parameter bank of the single-system kernels) rather than being formed per
+// round (the batch kernels, whose parameters are in global memory); same keys.
+template <int kLaw, bool kKeyTable>
 __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float dy, float dz,
                                             float4 vti, const float4* __restrict__ vt, int jj,
                                             float tagj, bool solid_pair, uint32_t idi, uint32_t step) {
@@ -57,14 +59,16 @@ __device__ __forceinline__ float4 pair_term(const StepParams& P, float dx, float
   if constexpr (kLaw == 0) {
     const float a = solid_pair ? P.a_fs : P.a_ff;
     const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
-    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.rkey);
+    const float xi = kKeyTable ? pair_noise(idi, id_of(tagj), step, P.sys, P.rkey)
+                               : pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
     return make_float4(w * (a - P.gamma * w * ev + P.sigma_rsqdt * xi), ex, ey, ez);
   } else {
     const float kr = solid_pair ? P.sph_kr_fs : P.sph_kr_ff;
     const float ka = solid_pair ? P.sph_ka_fs : P.sph_ka_ff;
     const float c = kr * spline_slope(r * P.sph_ihr) - ka * spline_slope(r * P.sph_iha);
     const float ev = ex * (vti.x - vtj.x) + ey * (vti.y - vtj.y) + ez * (vti.z - vtj.z);
-    const float xi = pair_noise(idi, id_of(tagj), step, P.sys, P.rkey);
+    const float xi = kKeyTable ? pair_noise(idi, id_of(tagj), step, P.sys, P.rkey)
+                               : pair_noise(idi, id_of(tagj), step, P.sys, P.seed_lo, P.seed_hi);
     return make_float4(fmaf(w, P.sigma_rsqdt * xi - P.gamma * w * ev, c), ex, ey, ez);
   }
 }
@@ -88,7 +92,7 @@ __device__ __forceinline__ void finish_target(const StepParams& P, const Arrays&
   if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&ctr->status, ST_NAN);
 }
 
-template <int kForceThreads, int kListCap, int kUnroll, int kLaw>
+template <int kForceThreads, int kListCap, int kUnroll, int kLaw, bool kKeyTable>
 __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* __restrict__ start,
                                            DevCounters* ctr, const Arrays& A, int i, float4 pi,
                                            int (*list)[kForceThreads],
@@ -220,7 +224,7 @@ __device__ __forceinline__ void force_body(const StepParams& P, const uint32_t* 
       const float dz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (!(r2 < 1.0f && r2 > 0.0f)) continue;
-      const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, is_solid(pj.w), idi, step);
+      const float4 t = pair_term<kLaw, kKeyTable>(P, dx, dy, dz, vti, vt, jj, pj.w, is_solid(pj.w), idi, step);
       fx = fmaf(t.x, t.y, fx);
       fy = fmaf(t.x, t.z, fy);
       fz = fmaf(t.x, t.w, fz);
@@ -259,7 +263,7 @@ __device__ __forceinline__ void half_row(int r, int* dy, int* dz) {
   *dz = r == 0 ? 0 : 1;
 }
 
-template <int kForceThreads, int kListCap, int kUnroll, int kLaw>
+template <int kForceThreads, int kListCap, int kUnroll, int kLaw, bool kKeyTable>
 __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_t* __restrict__ start,
                                               const Arrays& A, unsigned long long* __restrict__ facc,
                                               size_t stride, int i, float4 pi, DevCounters* ctr,
@@ -401,7 +405,7 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (!(r2 < 1.0f && r2 > 0.0f)) continue;
       const bool solid_j = is_solid(pj.w);
-      const float4 t = pair_term<kLaw>(P, dx, dy, dz, vti, vt, jj, pj.w, solid_i || solid_j, idi, step);
+      const float4 t = pair_term<kLaw, kKeyTable>(P, dx, dy, dz, vti, vt, jj, pj.w, solid_i || solid_j, idi, step);
       const float gx = t.x * t.y, gy = t.x * t.z, gz = t.x * t.w;
       fx += gx;
       fy += gy;
@@ -437,11 +441,11 @@ k_force_n3(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
   if (i >= n) return;
   const float4 pi = A.pos[i];
   if constexpr (kBatch) {
-    force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, A,
+    force_body_n3<kForceThreads, kListCap, kUnroll, kLaw, false>(S[sk].P, start_all + S[sk].cell_off, A,
                                                           facc, (size_t)n, i, pi, ctrs + sk, list,
                                                           seg_b, seg_e);
   } else {
-    force_body_n3<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, A, facc, (size_t)n, i, pi,
+    force_body_n3<kForceThreads, kListCap, kUnroll, kLaw, true>(P0, start_all, A, facc, (size_t)n, i, pi,
                                                           ctrs, list, seg_b, seg_e);
   }
 }
@@ -494,10 +498,10 @@ k_force(StepParams P0, const SysDesc* __restrict__ S, int nsys, Arrays A,
     return;
   }
   if constexpr (kBatch) {
-    force_body<kForceThreads, kListCap, kUnroll, kLaw>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,
+    force_body<kForceThreads, kListCap, kUnroll, kLaw, false>(S[sk].P, start_all + S[sk].cell_off, ctrs + sk,
                                                        A, i, pi, list, seg_b, seg_e, kick);
   } else {
-    force_body<kForceThreads, kListCap, kUnroll, kLaw>(P0, start_all, ctrs, A, i, pi, list, seg_b,
+    force_body<kForceThreads, kListCap, kUnroll, kLaw, true>(P0, start_all, ctrs, A, i, pi, list, seg_b,
                                                        seg_e, kick);
   }
 }
