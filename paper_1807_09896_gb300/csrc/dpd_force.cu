@@ -17,6 +17,8 @@
 // f_ji = -f_ij bit for bit.  The sum runs in a fixed order (cells in index
 // order, each cell in the fixed order the reorder gives it), which makes the
 // result independent of scheduling.
+#include <type_traits>
+
 #include "dpd_common.cuh"
 #include "dpd_launch.h"
 
@@ -318,106 +320,138 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
     }
   }
   float fx = 0.f, fy = 0.f, fz = 0.f;
-  int cnt = 0, seg = 0;
-  uint32_t j = 0, e = 0;
-  float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
-  float ux = tx, uy = ty, uz = tz;
-  bool more = true;
-  for (;;) {
-    // rounds of up to four candidates while the list has room for four
-    while (cnt <= kListCap - 4) {
-      if (j == e) {
-        if (seg == nseg) {
-          more = false;
-          break;
-        }
-        tx = pi.x; ty = pi.y; tz = pi.z;
-        sx = 0.f; sy = 0.f; sz = 0.f;
-        if (inner) {
-          // the range's bounds from the table; a shift only where a row wraps in y or z
-          // (the same sums the general path forms: t - L, or t + L)
-          j = seg_b[seg][threadIdx.x];
-          e = seg_e[seg][threadIdx.x];
-          if (seg > 0) {
-            int dy, dz;
-            half_row(seg - 1, &dy, &dz);
-            const int y = cy + dy;
-            ty = y < 0 ? pi.y : (y >= ncy ? pi.y - P.L[1] : pi.y);
-            sy = y < 0 ? P.L[1] : 0.f;
-            tz = cz + dz >= ncz ? pi.z - P.L[2] : pi.z;
+  // The walk, specialised on whether any lane of the warp is a solid particle (whose
+  // candidates must skip other solid particles: warps of fluid particles, nearly all,
+  // test no tags) and on whether every lane is away from the periodic seams (plain: each
+  // range comes from the table and needs no shift, and the pair loop takes plain
+  // differences).  Every form lists and evaluates the same pairs in the same order.
+  auto walk = [&](auto check_tag, auto plain) {
+    int cnt = 0, seg = 0;
+    uint32_t j = 0, e = 0;
+    float ux = pi.x, uy = pi.y, uz = pi.z;
+    bool more = true;
+    for (;;) {
+      // rounds of up to four candidates while the list has room for four
+      while (cnt <= kListCap - 4) {
+        if (j == e) {
+          if (seg == nseg) {
+            more = false;
+            break;
           }
-        } else if (seg == 0) {
-          j = (uint32_t)i + 1u;
-          e = __ldg(&start[own_row + cx + 1]);
-        } else if (!inner && seg == 1) {
-          int x = cx + 1;
-          if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
-          j = __ldg(&start[own_row + x]);
-          e = __ldg(&start[own_row + x + 1]);
-        } else {
-          int dy, dz;
-          half_row((seg - 2) / 3, &dy, &dz);
-          int z = cz + dz, y = cy + dy;
-          if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
-          if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
-          const int row = (z * ncy + y) * ncx;
-          int x = cx + (seg - 2) % 3 - 1;
-          if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
-          j = __ldg(&start[row + x]);
-          e = __ldg(&start[row + x + 1]);
+          if constexpr (decltype(plain)::value) {
+            j = seg_b[seg][threadIdx.x];
+            e = seg_e[seg][threadIdx.x];
+          } else {
+            float tx = pi.x, ty = pi.y, tz = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
+            if (inner) {
+              // the range's bounds from the table; a shift only where a row wraps in y or
+              // z (the same sums the general path forms: t - L, or t + L)
+              j = seg_b[seg][threadIdx.x];
+              e = seg_e[seg][threadIdx.x];
+              if (seg > 0) {
+                int dy, dz;
+                half_row(seg - 1, &dy, &dz);
+                const int y = cy + dy;
+                ty = y < 0 ? pi.y : (y >= ncy ? pi.y - P.L[1] : pi.y);
+                sy = y < 0 ? P.L[1] : 0.f;
+                tz = cz + dz >= ncz ? pi.z - P.L[2] : pi.z;
+              }
+            } else if (seg == 0) {
+              j = (uint32_t)i + 1u;
+              e = __ldg(&start[own_row + cx + 1]);
+            } else if (seg == 1) {
+              int x = cx + 1;
+              if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
+              j = __ldg(&start[own_row + x]);
+              e = __ldg(&start[own_row + x + 1]);
+            } else {
+              int dy, dz;
+              half_row((seg - 2) / 3, &dy, &dz);
+              int z = cz + dz, y = cy + dy;
+              if (z >= ncz) { z -= ncz; tz = pi.z - P.L[2]; }
+              if (y < 0) { y += ncy; sy = P.L[1]; } else if (y >= ncy) { y -= ncy; ty = pi.y - P.L[1]; }
+              const int row = (z * ncy + y) * ncx;
+              int x = cx + (seg - 2) % 3 - 1;
+              if (x < 0) { x += ncx; sx = P.L[0]; } else if (x >= ncx) { x -= ncx; tx = pi.x - P.L[0]; }
+              j = __ldg(&start[row + x]);
+              e = __ldg(&start[row + x + 1]);
+            }
+            ux = tx + sx;
+            uy = ty + sy;
+            uz = tz + sz;
+          }
+          ++seg;
+          // the round below takes the new segment's first candidates in the same pass
+          // (none if it is empty): lanes that change segments then cost the warp the
+          // switch, not a whole extra pass of rounds for the others
         }
-        ux = tx + sx;
-        uy = ty + sy;
-        uz = tz + sz;
-        ++seg;
-        // the round below takes the new segment's first candidates in the same pass
-        // (none if it is empty): lanes that change segments then cost the warp the
-        // switch, not a whole extra pass of rounds for the others
-      }
-      const uint32_t m = min(e - j, 4u);
-      if (m == 0u) continue;  // an empty segment: on to the next
-      // four consecutive slots from one address (the arrays carry kPosPad readable slots
-      // past the last particle); those past the segment's end never count
-      float4 q[4];
-      const float4* __restrict__ pj0 = pos + j;
+        const uint32_t m = min(e - j, 4u);
+        if (m == 0u) continue;  // an empty segment: on to the next
+        // four consecutive slots from one address (the arrays carry kPosPad readable slots
+        // past the last particle); those past the segment's end never count
+        float4 q[4];
+        const float4* __restrict__ pj0 = pos + j;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) q[u] = __ldg(pj0 + u);
-      // branch-free append: every slot is written, the count moves only on a hit (the
-      // round starts with room for four, so the writes stay inside the list)
+        for (int u = 0; u < 4; ++u) q[u] = __ldg(pj0 + u);
+        // branch-free append: every slot is written, the count moves only on a hit (the
+        // round starts with room for four, so the writes stay inside the list)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float dx = ux - q[u].x;
-        const float dy = uy - q[u].y;
-        const float dz = uz - q[u].z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        list[cnt][threadIdx.x] = (int)(j + u);
-        cnt += (u < (int)m) & (r2 < r2cut) & ((tag_of(q[u].w) & smask) == 0u);
+        for (int u = 0; u < 4; ++u) {
+          const float dx = ux - q[u].x;
+          const float dy = uy - q[u].y;
+          const float dz = uz - q[u].z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          list[cnt][threadIdx.x] = (int)(j + u);
+          if constexpr (decltype(check_tag)::value)
+            cnt += (u < (int)m) & (r2 < r2cut) & ((tag_of(q[u].w) & smask) == 0u);
+          else
+            cnt += (u < (int)m) & (r2 < r2cut);
+        }
+        j += m;
       }
-      j += m;
-    }
 #pragma unroll kUnroll
-    for (int k = 0; k < cnt; ++k) {
-      const int jj = list[k][threadIdx.x];
-      const float4 pj = __ldg(&pos[jj]);
-      const float dx = wrap_x ? min_image(pi.x, pj.x, P.L[0], P.halfL[0]) : pi.x - pj.x;
-      const float dy = wrap_y ? min_image(pi.y, pj.y, P.L[1], P.halfL[1]) : pi.y - pj.y;
-      const float dz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (!(r2 < 1.0f && r2 > 0.0f)) continue;
-      const bool solid_j = is_solid(pj.w);
-      const float4 t = pair_term<kLaw, kKeyTable>(P, dx, dy, dz, vti, vt, jj, pj.w, solid_i || solid_j, idi, step);
-      const float gx = t.x * t.y, gy = t.x * t.z, gz = t.x * t.w;
-      fx += gx;
-      fy += gy;
-      fz += gz;
-      if (!solid_j) {
-        fix_add(&facc[jj], -gx);
-        fix_add(&facc[stride + jj], -gy);
-        fix_add(&facc[2 * stride + jj], -gz);
+      for (int k = 0; k < cnt; ++k) {
+        const int jj = list[k][threadIdx.x];
+        const float4 pj = __ldg(&pos[jj]);
+        float dx, dy, dz;
+        if constexpr (decltype(plain)::value) {
+          dx = pi.x - pj.x;
+          dy = pi.y - pj.y;
+          dz = pi.z - pj.z;
+        } else {
+          dx = wrap_x ? min_image(pi.x, pj.x, P.L[0], P.halfL[0]) : pi.x - pj.x;
+          dy = wrap_y ? min_image(pi.y, pj.y, P.L[1], P.halfL[1]) : pi.y - pj.y;
+          dz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
+        }
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(r2 < 1.0f && r2 > 0.0f)) continue;
+        const bool solid_j = is_solid(pj.w);
+        const float4 t = pair_term<kLaw, kKeyTable>(P, dx, dy, dz, vti, vt, jj, pj.w, solid_i || solid_j, idi, step);
+        const float gx = t.x * t.y, gy = t.x * t.z, gz = t.x * t.w;
+        fx += gx;
+        fy += gy;
+        fz += gz;
+        if (!solid_j) {
+          fix_add(&facc[jj], -gx);
+          fix_add(&facc[stride + jj], -gy);
+          fix_add(&facc[2 * stride + jj], -gz);
+        }
       }
+      if (!more) break;  // the cells ran out
+      cnt = 0;
     }
-    if (!more) break;  // the cells ran out
-    cnt = 0;
+  };
+  const bool any_solid = __any_sync(wm, solid_i);
+  if (!(wrap_x || wrap_y || wrap_z)) {
+    if (any_solid)
+      walk(std::true_type{}, std::true_type{});
+    else
+      walk(std::false_type{}, std::true_type{});
+  } else {
+    if (any_solid)
+      walk(std::true_type{}, std::false_type{});
+    else
+      walk(std::false_type{}, std::false_type{});
   }
   // the own share goes to frc without an atomic (nothing else writes it): whoever reads
   // the sums adds it as one more integer term
