@@ -322,10 +322,13 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
   float fx = 0.f, fy = 0.f, fz = 0.f;
   // The walk, specialised on whether any lane of the warp is a solid particle (whose
   // candidates must skip other solid particles: warps of fluid particles, nearly all,
-  // test no tags) and on whether every lane is away from the periodic seams (plain: each
+  // test no tags) and on where the warp meets the periodic seams: nowhere (plain: each
   // range comes from the table and needs no shift, and the pair loop takes plain
-  // differences).  Every form lists and evaluates the same pairs in the same order.
-  auto walk = [&](auto check_tag, auto plain) {
+  // differences), only in x (the lanes away from the x seam take their ranges from the
+  // table unshifted, and only x needs the minimum image), or also in y or z (general).
+  // Every form lists and evaluates the same pairs in the same order.
+  auto walk = [&](auto check_tag, auto seams) {
+    constexpr int kSeams = decltype(seams)::value;  // 0 none, 1 x only, 2 any
     int cnt = 0, seg = 0;
     uint32_t j = 0, e = 0;
     float ux = pi.x, uy = pi.y, uz = pi.z;
@@ -338,7 +341,7 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
             more = false;
             break;
           }
-          if constexpr (decltype(plain)::value) {
+          if (kSeams == 0 || (kSeams == 1 && inner)) {
             j = seg_b[seg][threadIdx.x];
             e = seg_e[seg][threadIdx.x];
           } else {
@@ -414,8 +417,12 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
         const int jj = list[k][threadIdx.x];
         const float4 pj = __ldg(&pos[jj]);
         float dx, dy, dz;
-        if constexpr (decltype(plain)::value) {
+        if constexpr (kSeams == 0) {
           dx = pi.x - pj.x;
+          dy = pi.y - pj.y;
+          dz = pi.z - pj.z;
+        } else if constexpr (kSeams == 1) {
+          dx = min_image(pi.x, pj.x, P.L[0], P.halfL[0]);
           dy = pi.y - pj.y;
           dz = pi.z - pj.z;
         } else {
@@ -441,17 +448,25 @@ __device__ __forceinline__ void force_body_n3(const StepParams& P, const uint32_
       cnt = 0;
     }
   };
+  using NoSeam = std::integral_constant<int, 0>;
+  using XSeam = std::integral_constant<int, 1>;
+  using AnySeam = std::integral_constant<int, 2>;
   const bool any_solid = __any_sync(wm, solid_i);
-  if (!(wrap_x || wrap_y || wrap_z)) {
+  if (wrap_y || wrap_z) {
     if (any_solid)
-      walk(std::true_type{}, std::true_type{});
+      walk(std::true_type{}, AnySeam{});
     else
-      walk(std::false_type{}, std::true_type{});
+      walk(std::false_type{}, AnySeam{});
+  } else if (wrap_x) {
+    if (any_solid)
+      walk(std::true_type{}, XSeam{});
+    else
+      walk(std::false_type{}, XSeam{});
   } else {
     if (any_solid)
-      walk(std::true_type{}, std::false_type{});
+      walk(std::true_type{}, NoSeam{});
     else
-      walk(std::false_type{}, std::false_type{});
+      walk(std::false_type{}, NoSeam{});
   }
   // the own share goes to frc without an atomic (nothing else writes it): whoever reads
   // the sums adds it as one more integer term
