@@ -247,43 +247,43 @@ k_adj_force(StepParams P, const float4* __restrict__ pos, const float4* __restri
           const float ddz = wrap_z ? min_image(pi.z, pj.z, P.L[2], P.halfL[2]) : pi.z - pj.z;
           const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
           if (!(r2 < 1.0f && r2 > 0.0f)) continue;
-        const float inv_r = rsqrtf(r2);
-        const float r = r2 * inv_r;
-        const float w = 1.0f - r;
-        const float ex = ddx * inv_r, ey = ddy * inv_r, ez = ddz * inv_r;
-        const bool solid_j = is_solid(pj.w);
-        float ujx, ujy, ujz, a, Gx = Fx, Gy = Fy, Gz = Fz;
-        if (solid_j) {
-          ujx = P.vw[0]; ujy = P.vw[1]; ujz = P.vw[2];
-          a = P.a_fs;
-        } else {
-          const float4 vtj = vt[j];
-          ujx = vtj.x; ujy = vtj.y; ujz = vtj.z;
-          a = P.a_ff;
-          const float4 fbj = fbar[j], vbj = vbar[j];
-          const float kick_j = vtj.w == 0.0f ? P.half_dt : 0.0f;
-          Gx -= fbj.x + kick_j * vbj.x;
-          Gy -= fbj.y + kick_j * vbj.y;
-          Gz -= fbj.z + kick_j * vbj.z;
-        }
-        const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
-        const float eu = ex * ux + ey * uy + ez * uz;
-        const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.rkey);
-        const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
-        const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
-        const float eG = ex * Gx + ey * Gy + ez * Gz;
-        const float gw2 = P.gamma * w * w;
-        const float cu = -gw2 * eG * inv_r;
-        const float cm = m * inv_r;
-        Rx += m_r * eG * ex + cu * (ux - eu * ex) + cm * (Gx - eG * ex);
-        Ry += m_r * eG * ey + cu * (uy - eu * ey) + cm * (Gy - eG * ey);
-        Rz += m_r * eG * ez + cu * (uz - eu * ez) + cm * (Gz - eG * ez);
-        Ux -= gw2 * eG * ex;
-        Uy -= gw2 * eG * ey;
-        Uz -= gw2 * eG * ez;
-        const float eF = ex * Fx + ey * Fy + ez * Fz;
-        if (solid_j) ta += (double)(w * eF);
-        tg += (double)((-w * w * eu + tie_coef * w * xi) * eF);
+          const float inv_r = rsqrtf(r2);
+          const float r = r2 * inv_r;
+          const float w = 1.0f - r;
+          const float ex = ddx * inv_r, ey = ddy * inv_r, ez = ddz * inv_r;
+          const bool solid_j = is_solid(pj.w);
+          float ujx, ujy, ujz, a, Gx = Fx, Gy = Fy, Gz = Fz;
+          if (solid_j) {
+            ujx = P.vw[0]; ujy = P.vw[1]; ujz = P.vw[2];
+            a = P.a_fs;
+          } else {
+            const float4 vtj = vt[j];
+            ujx = vtj.x; ujy = vtj.y; ujz = vtj.z;
+            a = P.a_ff;
+            const float4 fbj = fbar[j], vbj = vbar[j];
+            const float kick_j = vtj.w == 0.0f ? P.half_dt : 0.0f;
+            Gx -= fbj.x + kick_j * vbj.x;
+            Gy -= fbj.y + kick_j * vbj.y;
+            Gz -= fbj.z + kick_j * vbj.z;
+          }
+          const float ux = vti.x - ujx, uy = vti.y - ujy, uz = vti.z - ujz;
+          const float eu = ex * ux + ey * uy + ez * uz;
+          const float xi = pair_noise(idi, id_of(pj.w), step, P.sys, P.rkey);
+          const float m = w * (a - P.gamma * w * eu + P.sigma_rsqdt * xi);
+          const float m_r = -a + 2.0f * P.gamma * w * eu - P.sigma_rsqdt * xi;
+          const float eG = ex * Gx + ey * Gy + ez * Gz;
+          const float gw2 = P.gamma * w * w;
+          const float cu = -gw2 * eG * inv_r;
+          const float cm = m * inv_r;
+          Rx += m_r * eG * ex + cu * (ux - eu * ex) + cm * (Gx - eG * ex);
+          Ry += m_r * eG * ey + cu * (uy - eu * ey) + cm * (Gy - eG * ey);
+          Rz += m_r * eG * ez + cu * (uz - eu * ez) + cm * (Gz - eG * ez);
+          Ux -= gw2 * eG * ex;
+          Uy -= gw2 * eG * ey;
+          Uz -= gw2 * eG * ez;
+          const float eF = ex * Fx + ey * Fy + ez * Fz;
+          if (solid_j) ta += (double)(w * eF);
+          tg += (double)((-w * w * eu + tie_coef * w * xi) * eF);
         }
         if (!more) break;
         cnt = 0;
